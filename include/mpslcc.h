@@ -1,0 +1,212 @@
+/*
+ * mpslcc.h -- C ABI of the GB300 (sm_103a) MPS-LCC hot-path library.
+ *
+ * Method: Sharma & Alavi, "Multireference linearized coupled cluster theory
+ * for strongly correlated systems using matrix product states".  The library
+ * builds matrix product operators for H and the Fink zeroth-order H0
+ * (Theory section, Eq. "part"), optimises a DMRG reference Phi0 (Eq. EH), and
+ * optimises the first-order wavefunction Phi1 as one MPS by minimising the
+ * Hylleraas functional (Eq. 1b, read consistently with Eq. 1) with two-site
+ * sweeps (Implementation section).  The hot operation is the local
+ * effective-Hamiltonian application ("sigma vector", Fig. 3): the derivative
+ * of the functional with respect to the local tensor.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Orbitals are the MPS sites 0..n_orb-1; local basis of one orbital:
+ *   0=|0>, 1=|up>, 2=|dn>, 3=|up dn> = a+_up a+_dn |0>; occupation-number
+ *   states are prod_p (a+_p,up)^n (a+_p,dn)^n |vac> in ascending p.
+ * - Quantum numbers are U(1)xU(1): (N, 2S_z).  Bond b (0..n_orb) sits left of
+ *   site b; its sector labels are left-cumulative (electrons and 2S_z of sites
+ *   0..b-1) and are listed in ascending (N, 2S_z) order.
+ * - Local (two-site) vector layout at position l (sites l, l+1): middle
+ *   sectors q ascending by (N, 2S_z); each sector is a row-major block with
+ *   rows = (s_l ascending, bond-l sector ascending, index within sector) and
+ *   cols = (s_l+1 ascending, bond-(l+2) sector ascending, index), restricted
+ *   to the local states each site allows.  A sector appears iff both its row
+ *   and column spaces are non-empty.
+ * - All arrays passed in are owned by the caller and only read during the
+ *   call; outputs go to caller-allocated buffers.  The context owns all its
+ *   device memory.  Functions never abort: on failure they return a status,
+ *   leave the context in its previous valid state, and record a message
+ *   readable with mpslcc_last_error().  One context per host thread.
+ * - Call order: create -> build_mpo -> (set_spaces) -> dmrg_reference ->
+ *   lcc_sweep -> energy.  Out-of-order calls return MPSLCC_E_STATE.
+ */
+#ifndef MPSLCC_H
+#define MPSLCC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpslcc_ctx mpslcc_ctx;
+
+typedef enum {
+  MPSLCC_OK = 0,
+  MPSLCC_E_ARG = 1,      /* invalid argument (sizes, symmetry, parity)     */
+  MPSLCC_E_STATE = 2,    /* call out of order                              */
+  MPSLCC_E_CUDA = 3,     /* CUDA / cuSOLVER error                          */
+  MPSLCC_E_NOMEM = 4,    /* device allocation failed                       */
+  MPSLCC_E_NOCONV = 5,   /* iterative solver did not converge; result kept */
+  MPSLCC_E_TIMEOUT = 6,  /* a bounded device wait gave up                  */
+  MPSLCC_E_INTERNAL = 7
+} mpslcc_status;
+
+typedef enum { MPSLCC_FP64 = 0, MPSLCC_TF32 = 1, MPSLCC_BF16 = 2 } mpslcc_prec;
+
+/* Operators for mpslcc_apply_heff / mpslcc_local_dim. */
+typedef enum {
+  MPSLCC_OP_H0_11 = 0,   /* P1^T H0 P1 : LCC matrix (without the -E0 shift)  */
+  MPSLCC_OP_H0_00 = 1,   /* P0^T H0 P0 : reference (DMRG) matrix             */
+  MPSLCC_OP_H_10 = 2,    /* P1^T H P0  : transition, input in Phi0's space   */
+  MPSLCC_OP_U_11 = 3,    /* P1^T U P1  : perturbation U = H - H0             */
+  MPSLCC_OP_S_10 = 4,    /* P1^T P0    : overlap, input in Phi0's space      */
+  MPSLCC_OP_H_11 = 5     /* P1^T H P1                                        */
+} mpslcc_op;
+
+typedef struct {
+  int device;            /* CUDA device ordinal; -1 = host-only context that
+                            can build and export MPOs but runs no kernels   */
+  void* stream;          /* cudaStream_t to run on; NULL = library-owned    */
+  int prec;              /* mpslcc_prec of the inner sigma products          */
+  double tol;            /* solver residual tolerance (relative)             */
+  int max_iter;          /* solver iteration cap per site                    */
+  int solver;            /* 0 = CG, 1 = MINRES, 2 = auto (CG, MINRES when a
+                            non-positive curvature is met)                   */
+  int davidson_max_subspace;
+  int refine_steps;      /* outer FP64 refinement steps (mixed precision)    */
+  unsigned long long seed;   /* initial-guess MPS seed                       */
+  int verbose;
+  /* Optional device allocator (e.g. a framework's caching allocator).  NULL
+     means cudaMallocAsync / cudaFreeAsync on the context stream. */
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, size_t bytes, void* user);
+  void* alloc_user;
+} mpslcc_opts;
+
+typedef struct {
+  double E0;        /* <Phi0|H|Phi0> of the reference                        */
+  double E2;        /* second order: Hylleraas minimum = <Phi0|H|Phi1>       */
+  double E3;        /* third order: <Phi1|U|Phi1> (Eq. 2, n = 1)             */
+  double E_lcc2;    /* E0 + E2                                               */
+  double E_lcc3;    /* E0 + E2 + E3                                          */
+  double hylleraas; /* last local Hylleraas value                           */
+  double overlap01; /* <Phi1|Phi0>                                           */
+  double norm1;     /* <Phi1|Phi1>                                           */
+  double max_discarded_weight;
+  int sweeps_done;
+} mpslcc_energies;
+
+typedef struct {
+  double sigma_flops;       /* algorithmic flops of all sigma products       */
+  double sigma_seconds;     /* device time inside sigma products             */
+  long long sigma_calls;
+  long long gemm_launches;
+  long long kernel_launches;
+  double env_flops;
+  double last_sweep_seconds;
+  double last_sweep_sigma_seconds;
+  double last_sweep_sigma_flops;
+  long long last_sweep_sigma_calls;
+  long long last_sweep_kernel_launches;
+  int max_bond_dim;
+  int mpo_max_bond;         /* largest MPO bond dimension (H)                */
+} mpslcc_stats;
+
+/* Fill *opts with defaults (device 0, FP64, tol 1e-10, max_iter 200, auto
+   solver, subspace 24, refine 4, seed 7). */
+void mpslcc_default_opts(mpslcc_opts* opts);
+
+/* Create / destroy a context.  Errors: E_ARG (NULL), E_CUDA (device). */
+mpslcc_status mpslcc_create(mpslcc_ctx** out, const mpslcc_opts* opts);
+mpslcc_status mpslcc_destroy(mpslcc_ctx* ctx);
+const char* mpslcc_last_error(const mpslcc_ctx* ctx);
+
+/* Theory section, Eq. "part": build the MPOs of H, H0 and U = H - H0 from the
+   one-body integrals h (n_orb x n_orb, row-major, symmetric) and chemists'
+   two-electron integrals V = (ij|kl) (n_orb^4, row-major, 8-fold symmetric),
+   H = sum h_ij a+_is a_js + 1/2 sum (ij|kl) a+_is a+_kt a_lt a_js, for
+   n_elec electrons with 2S_z = two_sz.  Errors: E_ARG if n_elec +- two_sz is
+   odd or out of range, or h / V lack their symmetry (tolerance 1e-10). */
+mpslcc_status mpslcc_build_mpo(mpslcc_ctx* ctx, const double* h, const double* V,
+                               int n_orb, int n_elec, int two_sz);
+
+/* Theory section (Fink partition): orbitals 0..n_core-1 are core (occupancy
+   2), the next n_active are active, the rest virtual (occupancy 0).  H0 keeps
+   the terms that move no electrons between the three sets.  Default after
+   build_mpo: n_core = 0, n_active = n_orb (H0 = H).  Rebuilds H0 and U;
+   discards any reference and first-order state. */
+mpslcc_status mpslcc_set_spaces(mpslcc_ctx* ctx, int n_core, int n_active);
+
+/* Eq. EH: two-site DMRG for the reference Phi0 (lowest eigenvector of H0 in
+   the reference class: core sites fixed to |up dn>, virtual sites to |0>),
+   bond dimension M0, n_sweeps left-right-left sweeps, Davidson local solver.
+   Writes E0 = <Phi0|H|Phi0>.  E_NOCONV if a local solve hit max_iter. */
+mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, double* E0_out);
+
+/* Eq. 1 (n = 1) in projector form: optimise Phi1 (bond dimension M1) by
+   minimising J = <Phi1|Q(H0-E0)Q|Phi1> - 2<Phi1|b>, b = -Q H Phi0, with
+   n_sweeps two-site sweeps; local linear solves by CG / MINRES with the
+   precision of opts.prec for inner products and FP64 residuals.  Writes E2
+   (the final Hylleraas value) to *E2_out.  order must be 1 (higher orders
+   return E_ARG).  The first call initialises Phi1 from opts.seed; later
+   calls continue from the current Phi1. */
+mpslcc_status mpslcc_lcc_sweep(mpslcc_ctx* ctx, int M1, int order, int n_sweeps, double* E2_out);
+
+/* Eq. 2: energies of the current states (E3 = <Phi1|U|Phi1> is evaluated on
+   demand). */
+mpslcc_status mpslcc_energy(mpslcc_ctx* ctx, mpslcc_energies* out);
+
+/* Local dimension of the two-site vector at position site (0..n_orb-2) for
+   operator op (output dimension for transition ops is the Phi1 space; *n_in
+   receives the input dimension, may be NULL). */
+mpslcc_status mpslcc_local_dim(mpslcc_ctx* ctx, int site, int op, long* n_out, long* n_in);
+
+/* Fig. 3 / Implementation section: sigma = P_bra^T O P_ket psi at two-site
+   position site, with environments built from the current MPS tensors (no
+   canonical form is assumed).  psi (n_in doubles) and sigma (n_out doubles)
+   are HOST arrays; prec selects FP64 or the TF32/BF16 tensor-core path.
+   Errors: E_ARG (sizes), E_STATE (MPS for op not present). */
+mpslcc_status mpslcc_apply_heff(mpslcc_ctx* ctx, int site, int op, const double* psi,
+                                double* sigma, long n_in, long n_out, int prec);
+
+/* Same with DEVICE pointers (FP64, on the context stream); no host copies. */
+mpslcc_status mpslcc_apply_heff_device(mpslcc_ctx* ctx, int site, int op, const double* d_psi,
+                                       double* d_sigma, long n_in, long n_out, int prec);
+
+/* Replace MPS `which` (0 = Phi0, 1 = Phi1) by caller data (checkpoint
+   restore and test input).  bond_nsec[b] (b = 0..n_sites) sector counts;
+   bond_qn: for every bond, 2*nsec ints (N, 2S_z) ascending; bond_dim: dims.
+   site_nblk[p] block counts; blk_desc: per block (ia, s, ib) as sector
+   indices of bond p, local state, sector index of bond p+1; data: the blocks
+   row-major [dim_a x dim_b] concatenated in the order given (n_data doubles).
+   Local states allowed at a site are those appearing in its blocks plus,
+   for which = 1, all four.  Errors: E_ARG (inconsistent quantum numbers). */
+mpslcc_status mpslcc_load_mps(mpslcc_ctx* ctx, int which, int n_sites, const int* bond_nsec,
+                              const int* bond_qn, const int* bond_dim, const int* site_nblk,
+                              const int* blk_desc, const double* data, long n_data);
+
+/* Export MPS `which` in the load format.  Call with NULL buffers to query
+   sizes (*n_int = ints needed in meta, *n_data = doubles); meta receives
+   bond_nsec | bond_qn | bond_dim | site_nblk | blk_desc concatenated. */
+mpslcc_status mpslcc_export_mps(mpslcc_ctx* ctx, int which, int* meta, long* n_int,
+                                double* data, long* n_data);
+
+/* MPO inspection (host only; works on a device = -1 context).  which: 0 = H,
+   1 = H0, 2 = U.  bond_dims receives n_orb+1 ints.  mpslcc_export_mpo_site
+   writes the site's nonzero entries as (w_left, w_right, s_out, s_in) ints
+   and values; call with NULL to query the count. */
+mpslcc_status mpslcc_mpo_bond_dims(mpslcc_ctx* ctx, int which, int* bond_dims);
+mpslcc_status mpslcc_export_mpo_site(mpslcc_ctx* ctx, int which, int site, int* idx,
+                                     double* val, long* count);
+
+mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out);
+mpslcc_status mpslcc_reset_stats(mpslcc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPSLCC_H */

@@ -1,0 +1,262 @@
+// Block-sparse MPS machinery on the GPU: fused spaces, environments, sigma
+// plans, truncation and the DMRG / LCC sweeps.
+#pragma once
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <map>
+#include <memory>
+#include <string>
+
+#include "common.hpp"
+#include "kernels.hpp"
+#include "mpo.hpp"
+#include "mpslcc.h"
+
+namespace mpslcc {
+
+struct Ctx;
+
+void cuda_check(cudaError_t e, const char* what);
+
+// Device buffer owned by a context (stream-ordered allocation).
+struct DBuf {
+  Ctx* c = nullptr;
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { swap(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); swap(o); }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void swap(DBuf& o) noexcept {
+    std::swap(c, o.c);
+    std::swap(p, o.p);
+    std::swap(bytes, o.bytes);
+  }
+  void alloc(Ctx* ctx, size_t nbytes);
+  void ensure(Ctx* ctx, size_t nbytes) {
+    if (bytes < nbytes) { release(); alloc(ctx, nbytes); }
+  }
+  void release();
+  double* d() const { return (double*)p; }
+};
+
+// A fused (bond x site) or (site x bond) space: sectors and their pieces.
+struct Piece { int sec, s, dim, off; };
+struct Fused {
+  std::vector<QN> q;
+  std::vector<int> d;
+  std::vector<std::vector<Piece>> pc;
+  int find(const QN& x) const {
+    auto it = std::lower_bound(q.begin(), q.end(), x);
+    if (it == q.end() || !(*it == x)) return -1;
+    return (int)(it - q.begin());
+  }
+  const Piece* piece(int f, int sec, int s) const {
+    for (const auto& p : pc[f])
+      if (p.sec == sec && p.s == s) return &p;
+    return nullptr;
+  }
+  long total() const {
+    long t = 0;
+    for (int v : d) t += v;
+    return t;
+  }
+};
+Fused fuse_left(const Sectors& b, const std::vector<int>& mask);   // key = q_bond + q_s
+Fused fuse_right(const std::vector<int>& mask, const Sectors& b);  // key = q_bond - q_s
+
+// Site tensor, kept in the left-fused layout (blocks per right-bond sector,
+// [dimFL x d_b] row-major) and/or the right-fused layout (blocks per
+// left-bond sector, [d_a x dimFR] row-major).
+struct SiteT {
+  DBuf lf, rf;
+  bool has_lf = false, has_rf = false;
+  std::vector<long> lf_off, rf_off;
+};
+
+struct MPS {
+  bool present = false;
+  int k = 0;
+  QN target;
+  std::vector<Sectors> bond;             // k+1
+  std::vector<std::vector<int>> mask;    // allowed local states per site
+  std::vector<SiteT> site;
+};
+
+struct EnvPair { int ib, ik, cls, nw; long off; };
+struct Env {
+  bool valid = false;
+  std::vector<EnvPair> pairs;
+  DBuf data;
+  long size = 0;
+};
+
+struct Family {
+  MPS* bra = nullptr;
+  MPS* ket = nullptr;
+  const Mpo* mpo = nullptr;
+  const DBuf* boxes = nullptr;   // device copy of the MPO's dense fusion boxes
+  std::vector<Env> L, R;         // per bond (k+1)
+  void reset(int k) {
+    L.clear();
+    R.clear();
+    L.resize(k + 1);
+    R.resize(k + 1);
+  }
+};
+
+// L'[w] of site p (w on MPO bond p+1), on the fused spaces FL_p.
+struct LeftFused {
+  int p = -1;
+  Fused FLb, FLk;
+  std::vector<int> kb, kk;            // key sectors (indices into FLb / FLk)
+  std::vector<int> kb_of, kk_of;      // FL index -> key index or -1
+  struct Seg { int cls, kidx, width, nw; long koff; };
+  std::vector<std::vector<Seg>> seg;  // per bra key
+  std::vector<long> K, off;           // per bra key
+  DBuf data;
+  long size = 0;
+  const Seg* find_seg(int bkey, int cls) const {
+    for (const auto& s : seg[bkey])
+      if (s.cls == cls) return &s;
+    return nullptr;
+  }
+};
+
+// R'[w] of site p (w on MPO bond p), on the fused spaces FR_p.
+struct RightFused {
+  int p = -1;
+  Fused FRb, FRk;
+  std::vector<int> kb, kk, kb_of, kk_of;
+  struct Stk { int kidx, cls, bidx, nw; long off; };
+  std::vector<Stk> stk;
+  std::map<std::pair<int, int>, int> sidx;  // (ket key, class) -> stack
+  DBuf data;
+  long size = 0;
+};
+
+// Two-site sigma plan at position l.
+struct SigmaPlan {
+  int l = -1;
+  Family* fam = nullptr;
+  LeftFused lf;
+  RightFused rf;
+  std::vector<QN> mid_b, mid_k;        // middle sectors (bra / ket)
+  std::vector<long> off_b, off_k;      // local-vector offsets
+  long nb = 0, nk = 0;
+  std::vector<long> tt_off;            // per bra middle
+  DBuf tt;
+  DBuf xin, yout;
+  DBuf tasks1, tasks2;
+  int n1 = 0, n2 = 0;
+  long long tiles1 = 0, tiles2 = 0;
+  bool split2 = false;
+  double flops = 0.0;                  // algorithmic flops of one application
+  // mixed precision copies (tensor-core path)
+  int lowp = -1;                       // prec of the low-precision copies
+  DBuf lcat_lp, rstk_lp, tt_lp, x_lp;  // operand copies
+  DBuf tc_tasks1, tc_tasks2;
+  int tc_n1 = 0, tc_n2 = 0;
+  long long tc_tiles1 = 0, tc_tiles2 = 0;
+};
+
+struct Stats {
+  double sigma_flops = 0, sigma_seconds = 0, env_flops = 0;
+  long long sigma_calls = 0, gemm_launches = 0, kernel_launches = 0;
+  double last_sweep_seconds = 0, last_sweep_sigma_seconds = 0, last_sweep_sigma_flops = 0;
+  long long last_sweep_sigma_calls = 0, last_sweep_kernel_launches = 0;
+  int max_bond_dim = 0;
+};
+
+struct Ctx {
+  // live device allocations (start -> bytes), used to validate every task's
+  // address range on the host before a launch
+  std::map<uintptr_t, size_t> allocs;
+  void check_range(const void* p, long long first, long long last, const char* what) const;
+
+  int device = 0;
+  bool host_only = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  mpslcc_opts opts{};
+  std::string err;
+  cusolverDnHandle_t solver = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // problem
+  int k = 0, n_elec = 0, two_sz = 0;
+  std::vector<double> h, V;
+  int n_core = 0, n_active = 0;
+  bool have_mpo = false;
+  Mpo mpo[4];              // H, H0, U, identity
+  DBuf boxes[4];
+  MPS phi0, phi1;
+  double E0 = 0, E2 = 0, E3 = 0, J = 0, ovl01 = 0, norm1 = 0, max_disc = 0;
+  bool have_E0 = false, have_E2 = false, e3_valid = false;
+  int sweeps_done = 0;
+  Stats st;
+
+  // families
+  Family f00;   // <Phi0|H0|Phi0>
+  Family f11;   // <Phi1|H0|Phi1>
+  Family f10;   // <Phi1|H|Phi0>
+  Family s10;   // <Phi1|Phi0>
+  Family u11;   // <Phi1|U|Phi1>
+  Family h11;   // <Phi1|H|Phi1>
+
+  // scratch
+  DBuf red, red_out, gtask, ctask;
+  DBuf eig_work, eig_w, eig_info;
+  DBuf scratch_a, scratch_b;
+
+  cudaStream_t s() const { return stream; }
+};
+
+// ---- engine entry points (engine.cpp / sweep.cpp) ----
+void upload_boxes(Ctx& c, int which);
+void run_gemms(Ctx& c, std::vector<GemmTask>& t);
+void validate_gemm(const Ctx& c, const GemmTask& t);
+void validate_copy(const Ctx& c, const CopyTask& t);
+void run_copies(Ctx& c, std::vector<CopyTask>& t);
+double dev_dot(Ctx& c, const double* x, const double* y, long n);
+
+void ensure_lf(Ctx& c, MPS& m, int p);
+void ensure_rf(Ctx& c, MPS& m, int p);
+void set_site_lf(Ctx& c, MPS& m, int p, DBuf&& data);
+void set_site_rf(Ctx& c, MPS& m, int p, DBuf&& data);
+std::vector<long> layout_offsets(const MPS& m, int p, int layout, long* total);
+
+void boundary_envs(Ctx& c, Family& F);
+void build_left_env(Ctx& c, Family& F, int p);    // L[p+1] from L[p] and site p
+void build_right_env(Ctx& c, Family& F, int p);   // R[p] from R[p+1] and site p
+void make_left_fused(Ctx& c, Family& F, int p, const std::vector<QN>& kb, const std::vector<QN>& kk,
+                     LeftFused& lf);
+void make_right_fused(Ctx& c, Family& F, int p, const std::vector<QN>& kb, const std::vector<QN>& kk,
+                      RightFused& rf);
+void env_update_left(Ctx& c, Family& F, int p, const LeftFused& lf);
+void env_update_right(Ctx& c, Family& F, int p, const RightFused& rf);
+
+void two_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long>& off, long& n);
+void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P);
+void sigma_apply(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec);
+void sigma_diag(Ctx& c, SigmaPlan& P, double* diag);
+void form_two_site(Ctx& c, MPS& m, int l, double* psi);   // psi in m's middle layout
+void ensure_envs(Ctx& c, Family& F, int l);
+
+// tensor-core path (tc_gemm.cu)
+void tc_prepare(Ctx& c, SigmaPlan& P, int prec);
+void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y);
+
+// sweeps (sweep.cpp)
+void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed);
+double dmrg_reference(Ctx& c, int M0, int n_sweeps);
+double lcc_sweeps(Ctx& c, int M1, int n_sweeps);
+void compute_e3(Ctx& c);
+
+}  // namespace mpslcc

@@ -1,0 +1,792 @@
+// Sweep algorithms (Implementation section): at each two-site position the
+// functional is quadratic in the local tensor; the DMRG reference (Eq. EH)
+// solves a local eigenproblem (Davidson), the first-order LCC wavefunction
+// (Eq. 1 / Eq. 1b) a local linear system (conjugate gradients, MINRES when
+// the local matrix is indefinite).  After each local solve the two-site
+// tensor is split by the density-matrix eigendecomposition (FP64 cuSOLVER)
+// keeping at most M states, and the environments are renormalised.
+#include <cmath>
+#include <cstring>
+#include <random>
+
+#include "engine.hpp"
+
+namespace mpslcc {
+
+namespace {
+
+struct Vec {
+  DBuf b;
+  long n = 0;
+  void alloc(Ctx& c, long n_) {
+    n = n_;
+    b.ensure(&c, std::max(n_, 1L) * sizeof(double));
+  }
+  double* d() const { return b.d(); }
+};
+
+double vnorm(Ctx& c, const Vec& v) { return std::sqrt(std::max(0.0, dev_dot(c, v.d(), v.d(), v.n))); }
+
+void copyv(Ctx& c, double* dst, const double* src, long n) {
+  if (n > 0) cuda_check(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "copy vec");
+}
+
+// multidot against m stored vectors, results on host
+std::vector<double> multidot(Ctx& c, const double* V, long ld, int m, const double* x, long n) {
+  std::vector<double> out(m);
+  if (m == 0) return out;
+  c.red.ensure(&c, std::max<size_t>(4096, (size_t)m * 64) * sizeof(double));
+  c.red_out.ensure(&c, std::max(256, m) * sizeof(double));
+  launch_multidot(n, m, V, ld, x, c.red_out.d(), c.red.d(), c.s());
+  c.st.kernel_launches += 2;
+  cuda_check(cudaMemcpyAsync(out.data(), c.red_out.p, m * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "mdot");
+  cuda_check(cudaStreamSynchronize(c.s()), "mdot sync");
+  return out;
+}
+
+// out = sum_j coef[j] V_j
+void lincomb(Ctx& c, const double* V, long ld, int m, const std::vector<double>& coef, double* out, long n) {
+  c.red_out.ensure(&c, std::max(256, m) * sizeof(double));
+  cuda_check(cudaMemcpyAsync(c.red_out.p, coef.data(), m * sizeof(double), cudaMemcpyHostToDevice, c.s()), "coef");
+  launch_lincomb(n, m, V, ld, c.red_out.d(), out, c.s());
+  c.st.kernel_launches++;
+  cuda_check(cudaStreamSynchronize(c.s()), "lincomb sync");
+}
+
+// Symmetric eigenproblem of a small dense matrix (cyclic Jacobi).
+void jacobi_eigh(int n, std::vector<double>& A, std::vector<double>& w, std::vector<double>& Vm) {
+  Vm.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Vm[i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += A[i * n + j] * A[i * n + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double apq = A[p * n + q];
+        if (std::fabs(apq) < 1e-300) continue;
+        double app = A[p * n + p], aqq = A[q * n + q];
+        double theta = (aqq - app) / (2 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1));
+        double cs = 1 / std::sqrt(t * t + 1), sn = t * cs;
+        for (int k = 0; k < n; ++k) {
+          double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = cs * akp - sn * akq;
+          A[k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = cs * apk - sn * aqk;
+          A[q * n + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          double vkp = Vm[k * n + p], vkq = Vm[k * n + q];
+          Vm[k * n + p] = cs * vkp - sn * vkq;
+          Vm[k * n + q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[i * n + i];
+}
+
+void sigma_timed(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
+  cudaEventRecord(c.ev0, c.s());
+  sigma_apply(c, P, x, y, prec);
+  cudaEventRecord(c.ev1, c.s());
+  cuda_check(cudaEventSynchronize(c.ev1), "sigma sync");
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+  c.st.sigma_seconds += ms * 1e-3;
+}
+
+// Davidson for the lowest eigenpair of the local H_eff (reference, Eq. EH).
+double davidson(Ctx& c, SigmaPlan& P, double* x, long n, const double* diag, double tol, int maxit, int maxsub,
+                bool* converged) {
+  maxsub = std::max(4, std::min(maxsub, (int)std::max(1L, n)));
+  DBuf Vb, AVb;
+  Vb.alloc(&c, (size_t)maxsub * n * sizeof(double));
+  AVb.alloc(&c, (size_t)maxsub * n * sizeof(double));
+  Vec r, t, xs;
+  r.alloc(c, n);
+  t.alloc(c, n);
+  xs.alloc(c, n);
+  double* V = Vb.d();
+  double* AV = AVb.d();
+  double nx = std::sqrt(std::max(0.0, dev_dot(c, x, x, n)));
+  if (nx < 1e-14) {
+    launch_fill(n, 1.0, x, c.s());
+    nx = std::sqrt((double)n);
+  }
+  copyv(c, V, x, n);
+  launch_scale(n, 1.0 / nx, V, c.s());
+  sigma_timed(c, P, V, AV, MPSLCC_FP64);
+  int m = 1;
+  std::vector<double> Hs(1, dev_dot(c, V, AV, n));
+  double theta = Hs[0];
+  *converged = false;
+  std::vector<double> y(1, 1.0);
+  for (int it = 0; it < maxit; ++it) {
+    std::vector<double> A = Hs, w, Ym;
+    jacobi_eigh(m, A, w, Ym);
+    int imin = 0;
+    for (int i = 1; i < m; ++i)
+      if (w[i] < w[imin]) imin = i;
+    theta = w[imin];
+    y.assign(m, 0.0);
+    for (int i = 0; i < m; ++i) y[i] = Ym[i * m + imin];
+    lincomb(c, V, n, m, y, xs.d(), n);
+    lincomb(c, AV, n, m, y, r.d(), n);
+    launch_axpy(n, -theta, xs.d(), r.d(), c.s());
+    double rn = vnorm(c, r);
+    if (rn < tol || n == 1 || m >= n) {
+      *converged = true;
+      break;
+    }
+    launch_precond(n, r.d(), diag, theta, 1e-4, t.d(), 0, c.s());
+    for (int pass = 0; pass < 2; ++pass) {
+      std::vector<double> pr = multidot(c, V, n, m, t.d(), n);
+      for (auto& v : pr) v = -v;
+      lincomb(c, V, n, m, pr, r.d(), n);
+      launch_axpy(n, 1.0, r.d(), t.d(), c.s());
+    }
+    double tn = vnorm(c, t);
+    if (tn < 1e-12) {
+      *converged = rn < 1e3 * tol;
+      break;
+    }
+    launch_scale(n, 1.0 / tn, t.d(), c.s());
+    if (m == maxsub) {
+      // restart from the current Ritz vector
+      copyv(c, V, xs.d(), n);
+      lincomb(c, AV, n, m, y, r.d(), n);
+      copyv(c, AV, r.d(), n);
+      m = 1;
+      Hs.assign(1, theta);
+      std::vector<double> pr = multidot(c, V, n, 1, t.d(), n);
+      launch_axpy(n, -pr[0], V, t.d(), c.s());
+      double tn2 = vnorm(c, t);
+      if (tn2 < 1e-12) { *converged = true; break; }
+      launch_scale(n, 1.0 / tn2, t.d(), c.s());
+    }
+    copyv(c, V + (long)m * n, t.d(), n);
+    sigma_timed(c, P, V + (long)m * n, AV + (long)m * n, MPSLCC_FP64);
+    std::vector<double> col = multidot(c, V, n, m + 1, AV + (long)m * n, n);
+    std::vector<double> H2((size_t)(m + 1) * (m + 1));
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) H2[i * (m + 1) + j] = Hs[i * m + j];
+    for (int i = 0; i <= m; ++i) {
+      H2[i * (m + 1) + m] = col[i];
+      H2[m * (m + 1) + i] = col[i];
+    }
+    Hs = H2;
+    ++m;
+  }
+  copyv(c, x, xs.d(), n);
+  return theta;
+}
+
+// Q v = v - u (u.v)  (u normalised, or null)
+void project(Ctx& c, const double* u, double* v, long n) {
+  if (!u) return;
+  double a = dev_dot(c, u, v, n);
+  launch_axpy(n, -a, u, v, c.s());
+}
+
+struct LinOp {
+  SigmaPlan* P;
+  double shift;
+  const double* u;
+  Vec q;
+  void apply(Ctx& c, const double* v, double* out, int prec) {
+    long n = P->nb;
+    q.alloc(c, n);
+    copyv(c, q.d(), v, n);
+    project(c, u, q.d(), n);
+    sigma_timed(c, *P, q.d(), out, prec);
+    launch_axpy(n, -shift, q.d(), out, c.s());
+    project(c, u, out, n);
+  }
+};
+
+// Preconditioned CG (MINRES when a non-positive curvature appears) for
+// A x = b, A = Q (H_eff - shift) Q.  Returns the final residual norm.
+double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* diag, long n, double tol, int maxit,
+                    int prec, int* iters, bool* indefinite) {
+  Vec r, z, p, Ap;
+  r.alloc(c, n);
+  z.alloc(c, n);
+  p.alloc(c, n);
+  Ap.alloc(c, n);
+  double bn = std::sqrt(std::max(0.0, dev_dot(c, b, b, n)));
+  if (bn < 1e-300) {
+    launch_fill(n, 0.0, x, c.s());
+    *iters = 0;
+    return 0.0;
+  }
+  project(c, A.u, x, n);
+  A.apply(c, x, Ap.d(), prec);
+  copyv(c, r.d(), b, n);
+  launch_axpy(n, -1.0, Ap.d(), r.d(), c.s());
+  auto precond = [&](const double* in, double* out) {
+    launch_precond(n, in, diag, A.shift, 1e-2, out, 1, c.s());
+    project(c, A.u, out, n);
+  };
+  precond(r.d(), z.d());
+  copyv(c, p.d(), z.d(), n);
+  double rz = dev_dot(c, r.d(), z.d(), n);
+  double rn = vnorm(c, r);
+  int it = 0;
+  *indefinite = false;
+  while (rn > tol * bn && it < maxit) {
+    A.apply(c, p.d(), Ap.d(), prec);
+    double pAp = dev_dot(c, p.d(), Ap.d(), n);
+    if (pAp <= 0) {
+      *indefinite = true;
+      break;
+    }
+    double alpha = rz / pAp;
+    launch_axpy(n, alpha, p.d(), x, c.s());
+    launch_axpy(n, -alpha, Ap.d(), r.d(), c.s());
+    precond(r.d(), z.d());
+    double rz2 = dev_dot(c, r.d(), z.d(), n);
+    launch_axpby(n, 1.0, z.d(), rz2 / rz, p.d(), c.s());
+    rz = rz2;
+    rn = vnorm(c, r);
+    ++it;
+  }
+  if (*indefinite) {
+    // MINRES on the same (symmetric, possibly indefinite) operator, from x
+    Vec v0, v1, w0, w1, w2, av;
+    v0.alloc(c, n); v1.alloc(c, n); w0.alloc(c, n); w1.alloc(c, n); w2.alloc(c, n); av.alloc(c, n);
+    A.apply(c, x, av.d(), prec);
+    copyv(c, v1.d(), b, n);
+    launch_axpy(n, -1.0, av.d(), v1.d(), c.s());
+    double beta = vnorm(c, v1), eta = beta;
+    launch_fill(n, 0.0, v0.d(), c.s());
+    launch_fill(n, 0.0, w0.d(), c.s());
+    launch_fill(n, 0.0, w1.d(), c.s());
+    double gam0 = 1, gam1 = 1, sig0 = 0, sig1 = 0, betaold = 0;
+    if (beta > 0) launch_scale(n, 1.0 / beta, v1.d(), c.s());
+    rn = beta;
+    while (rn > tol * bn && it < maxit && beta > 1e-300) {
+      A.apply(c, v1.d(), av.d(), prec);
+      double alpha = dev_dot(c, v1.d(), av.d(), n);
+      launch_axpy(n, -alpha, v1.d(), av.d(), c.s());
+      launch_axpy(n, -beta, v0.d(), av.d(), c.s());
+      betaold = beta;
+      beta = vnorm(c, av);
+      double d0 = gam1 * alpha - gam0 * sig1 * betaold;
+      double r1 = std::sqrt(d0 * d0 + beta * beta);
+      double r2 = sig1 * alpha + gam0 * gam1 * betaold;
+      double r3 = sig0 * betaold;
+      if (r1 < 1e-300) break;
+      gam0 = gam1; sig0 = sig1;
+      gam1 = d0 / r1; sig1 = beta / r1;
+      // w2 = (v1 - r3 w0 - r2 w1) / r1
+      copyv(c, w2.d(), v1.d(), n);
+      launch_axpy(n, -r3, w0.d(), w2.d(), c.s());
+      launch_axpy(n, -r2, w1.d(), w2.d(), c.s());
+      launch_scale(n, 1.0 / r1, w2.d(), c.s());
+      launch_axpy(n, gam1 * eta, w2.d(), x, c.s());
+      eta = -sig1 * eta;
+      rn = std::fabs(eta);
+      std::swap(w0.b, w1.b);
+      std::swap(w1.b, w2.b);
+      std::swap(v0.b, v1.b);
+      if (beta > 0) {
+        copyv(c, v1.d(), av.d(), n);
+        launch_scale(n, 1.0 / beta, v1.d(), c.s());
+      }
+      ++it;
+    }
+    project(c, A.u, x, n);
+    A.apply(c, x, Ap.d(), prec);
+    copyv(c, r.d(), b, n);
+    launch_axpy(n, -1.0, Ap.d(), r.d(), c.s());
+    rn = vnorm(c, r);
+  }
+  *iters = it;
+  return rn;
+}
+
+// Split the two-site vector at position l of MPS m keeping <= M states.
+double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_right) {
+  std::vector<QN> mid;
+  std::vector<long> off;
+  long n_loc;
+  two_site_middle(m, l, mid, off, n_loc);
+  Fused FL = fuse_left(m.bond[l], m.mask[l]);
+  Fused FR = fuse_right(m.mask[l + 1], m.bond[l + 2]);
+  int ns = (int)mid.size();
+  std::vector<int> dl(ns), dr(ns), nd(ns);
+  std::vector<long> roff(ns), woff(ns);
+  long rtot = 0, wtot = 0;
+  int nmax = 1;
+  for (int i = 0; i < ns; ++i) {
+    dl[i] = FL.d[FL.find(mid[i])];
+    dr[i] = FR.d[FR.find(mid[i])];
+    nd[i] = moving_right ? dl[i] : dr[i];
+    roff[i] = rtot;
+    woff[i] = wtot;
+    rtot += (long)nd[i] * nd[i];
+    wtot += nd[i];
+    nmax = std::max(nmax, nd[i]);
+  }
+  DBuf rho, w;
+  rho.alloc(&c, std::max(rtot, 1L) * sizeof(double));
+  w.alloc(&c, std::max(wtot, 1L) * sizeof(double));
+  std::vector<GemmTask> gt;
+  for (int i = 0; i < ns; ++i) {
+    GemmTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.A = psi + off[i];
+    t.B = psi + off[i];
+    t.C = rho.d() + roff[i];
+    t.batch = 1;
+    t.alpha = 1.0;
+    t.ksplit = 1;
+    if (moving_right) {  // rho = psi psi^T
+      t.m = dl[i]; t.n = dl[i]; t.k = dr[i];
+      t.lda = dr[i]; t.ldb = dr[i]; t.ldc = dl[i];
+      t.flags = GEMM_TB;
+    } else {  // rho = psi^T psi
+      t.m = dr[i]; t.n = dr[i]; t.k = dl[i];
+      t.lda = dr[i]; t.ldb = dr[i]; t.ldc = dr[i];
+      t.flags = GEMM_TA;
+    }
+    gt.push_back(t);
+  }
+  run_gemms(c, gt);
+  // FP64 eigendecompositions (cuSOLVER), eigenvalues ascending
+  int lwork = 0;
+  for (int i = 0; i < ns; ++i) {
+    int lw = 0;
+    cusolverDnDsyevd_bufferSize(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i], rho.d() + roff[i],
+                                nd[i], w.d() + woff[i], &lw);
+    lwork = std::max(lwork, lw);
+  }
+  c.eig_work.ensure(&c, (size_t)std::max(lwork, 1) * sizeof(double));
+  c.eig_info.ensure(&c, sizeof(int) * 4);
+  for (int i = 0; i < ns; ++i) {
+    c.check_range(rho.d() + roff[i], 0, (long long)nd[i] * nd[i] - 1, "eigh matrix");
+    c.check_range(w.d() + woff[i], 0, nd[i] - 1, "eigh values");
+    cusolverStatus_t st = cusolverDnDsyevd(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i],
+                                           rho.d() + roff[i], nd[i], w.d() + woff[i], c.eig_work.d(), lwork,
+                                           (int*)c.eig_info.p);
+    MPSLCC_REQUIRE(st == CUSOLVER_STATUS_SUCCESS, ST_CUDA, "cusolverDnDsyevd failed");
+    c.st.kernel_launches++;
+  }
+  std::vector<double> hw(std::max(wtot, 1L));
+  cuda_check(cudaMemcpyAsync(hw.data(), w.p, wtot * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "eig d2h");
+  cuda_check(cudaStreamSynchronize(c.s()), "eig sync");
+  // keep the M largest weights; ties by (sector, index)
+  struct Ent { double v; int s, j; };
+  std::vector<Ent> all;
+  double total = 0;
+  for (int i = 0; i < ns; ++i)
+    for (int j = 0; j < nd[i]; ++j) {
+      double v = hw[woff[i] + nd[i] - 1 - j];  // j-th largest in sector i
+      all.push_back({v, i, j});
+      total += std::max(v, 0.0);
+    }
+  std::stable_sort(all.begin(), all.end(), [](const Ent& a, const Ent& b) {
+    if (a.v != b.v) return a.v > b.v;
+    if (a.s != b.s) return a.s < b.s;
+    return a.j < b.j;
+  });
+  std::vector<int> keep(ns, 0);
+  double kept = 0;
+  for (size_t e = 0; e < all.size() && (int)e < M; ++e) {
+    keep[all[e].s]++;
+    kept += std::max(all[e].v, 0.0);
+  }
+  double disc = total > 0 ? std::max(0.0, (total - kept) / total) : 0.0;
+  // new bond l+1
+  Sectors nb;
+  std::vector<int> sidx;
+  for (int i = 0; i < ns; ++i)
+    if (keep[i] > 0) {
+      nb.q.push_back(mid[i]);
+      nb.d.push_back(keep[i]);
+      sidx.push_back(i);
+    }
+  MPSLCC_REQUIRE(nb.size() > 0, ST_INTERNAL, "truncation kept no states");
+  m.bond[l + 1] = nb;
+  long isz = 0, csz = 0;
+  for (size_t t = 0; t < sidx.size(); ++t) {
+    int i = sidx[t];
+    isz += (long)nd[i] * keep[i];
+    csz += (long)(moving_right ? dr[i] : dl[i]) * keep[i];
+  }
+  DBuf iso, cen;
+  iso.alloc(&c, std::max(isz, 1L) * sizeof(double));
+  cen.alloc(&c, std::max(csz, 1L) * sizeof(double));
+  std::vector<GemmTask> ct;
+  long io = 0, co = 0;
+  for (size_t t = 0; t < sidx.size(); ++t) {
+    int i = sidx[t];
+    int kq = keep[i];
+    c.check_range(iso.d() + io, 0, (long long)nd[i] * kq - 1, "eigvecs");
+    launch_take_eigvecs(rho.d() + roff[i], nd[i], kq, moving_right ? 0 : 1, iso.d() + io, c.s());
+    c.st.kernel_launches++;
+    GemmTask g;
+    std::memset(&g, 0, sizeof(g));
+    g.batch = 1;
+    g.alpha = 1.0;
+    g.ksplit = 1;
+    if (moving_right) {  // C = A^T psi  [kq x dr]
+      g.A = iso.d() + io; g.B = psi + off[i]; g.C = cen.d() + co;
+      g.m = kq; g.n = dr[i]; g.k = dl[i];
+      g.lda = kq; g.ldb = dr[i]; g.ldc = dr[i];
+      g.flags = GEMM_TA;
+      co += (long)kq * dr[i];
+    } else {  // C = psi B^T  [dl x kq]
+      g.A = psi + off[i]; g.B = iso.d() + io; g.C = cen.d() + co;
+      g.m = dl[i]; g.n = kq; g.k = dr[i];
+      g.lda = dr[i]; g.ldb = dr[i]; g.ldc = kq;
+      g.flags = GEMM_TB;
+      co += (long)dl[i] * kq;
+    }
+    ct.push_back(g);
+    io += (long)nd[i] * kq;
+  }
+  run_gemms(c, ct);
+  if (moving_right) {
+    set_site_lf(c, m, l, std::move(iso));
+    set_site_rf(c, m, l + 1, std::move(cen));
+  } else {
+    set_site_rf(c, m, l + 1, std::move(iso));
+    set_site_lf(c, m, l, std::move(cen));
+  }
+  int bd = nb.total();
+  c.st.max_bond_dim = std::max(c.st.max_bond_dim, bd);
+  return disc;
+}
+
+void invalidate_site(Family& F, int p) {
+  int k = (int)F.L.size() - 1;
+  if (k < 0) return;
+  for (int b = p + 1; b <= k; ++b) F.L[b].valid = false;
+  for (int b = 0; b <= p; ++b) F.R[b].valid = false;
+  for (int b = p + 1; b <= k; ++b) F.L[b].data.release();
+  for (int b = 1; b <= p; ++b) F.R[b].data.release();
+}
+
+void bind(Ctx& c, Family& F, MPS* bra, int mpo, MPS* ket) {
+  F.bra = bra;
+  F.ket = ket;
+  F.mpo = &c.mpo[mpo];
+  F.boxes = &c.boxes[mpo];
+  boundary_envs(c, F);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed) {
+  int k = c.k;
+  m = MPS();
+  m.k = k;
+  m.target = QN(c.n_elec, c.two_sz);
+  m.mask.resize(k);
+  for (int p = 0; p < k; ++p) {
+    if (frozen && p < c.n_core) m.mask[p] = {3};
+    else if (frozen && p >= c.n_core + c.n_active) m.mask[p] = {0};
+    else m.mask[p] = {0, 1, 2, 3};
+  }
+  // sector counts from both ends
+  std::vector<std::map<QN, double>> left(k + 1), right(k + 1);
+  left[0][QN(0, 0)] = 1;
+  for (int p = 0; p < k; ++p)
+    for (auto& kv : left[p])
+      for (int s : m.mask[p]) left[p + 1][kv.first + LOCAL_Q[s]] += kv.second;
+  right[k][m.target] = 1;
+  for (int p = k - 1; p >= 0; --p)
+    for (auto& kv : right[p + 1])
+      for (int s : m.mask[p]) right[p][kv.first - LOCAL_Q[s]] += kv.second;
+  m.bond.assign(k + 1, Sectors());
+  for (int b = 0; b <= k; ++b) {
+    std::vector<std::pair<QN, double>> v;
+    double tot = 0;
+    for (auto& kv : left[b]) {
+      auto it = right[b].find(kv.first);
+      if (it == right[b].end()) continue;
+      double d = std::min(kv.second, it->second);
+      v.push_back({kv.first, d});
+      tot += std::min(d, (double)M);
+    }
+    for (auto& pr : v) {
+      double d = std::min(pr.second, (double)M);
+      if (tot > M) d = std::floor(d * M / tot);
+      d = std::max(1.0, std::min(d, pr.second));
+      m.bond[b].q.push_back(pr.first);
+      m.bond[b].d.push_back((int)d);
+    }
+  }
+  // consistency: every sector must be reachable from both sides with enough rows / cols
+  for (int iter = 0; iter < 4; ++iter) {
+    for (int p = k - 1; p >= 0; --p) {
+      Sectors nb;
+      for (int i = 0; i < m.bond[p].size(); ++i) {
+        long cap = 0;
+        for (int s : m.mask[p]) {
+          int j = m.bond[p + 1].find(m.bond[p].q[i] + LOCAL_Q[s]);
+          if (j >= 0) cap += m.bond[p + 1].d[j];
+        }
+        int d = (int)std::min<long>(m.bond[p].d[i], cap);
+        if (d > 0) { nb.q.push_back(m.bond[p].q[i]); nb.d.push_back(d); }
+      }
+      m.bond[p] = nb;
+    }
+    for (int p = 0; p < k; ++p) {
+      Sectors nb;
+      for (int j = 0; j < m.bond[p + 1].size(); ++j) {
+        long cap = 0;
+        for (int s : m.mask[p]) {
+          int i = m.bond[p].find(m.bond[p + 1].q[j] - LOCAL_Q[s]);
+          if (i >= 0) cap += m.bond[p].d[i];
+        }
+        int d = (int)std::min<long>(m.bond[p + 1].d[j], cap);
+        if (d > 0) { nb.q.push_back(m.bond[p + 1].q[j]); nb.d.push_back(d); }
+      }
+      m.bond[p + 1] = nb;
+    }
+  }
+  MPSLCC_REQUIRE(m.bond[0].size() == 1 && m.bond[k].size() == 1, ST_ARG,
+                 "no MPS with the requested electron number / spin fits the orbital partition");
+  m.site.clear();
+  m.site.resize(k);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (int p = 0; p < k; ++p) {
+    long tot;
+    std::vector<long> off = layout_offsets(m, p, 1, &tot);
+    Fused FR = fuse_right(m.mask[p], m.bond[p + 1]);
+    std::vector<double> host(std::max(tot, 1L), 0.0);
+    for (int i = 0; i < m.bond[p].size(); ++i) {
+      int f = FR.find(m.bond[p].q[i]);
+      if (f < 0) continue;
+      int rows = m.bond[p].d[i], cols = FR.d[f];
+      double* B = host.data() + off[i];
+      for (long e = 0; e < (long)rows * cols; ++e) B[e] = nd(rng);
+      // modified Gram-Schmidt on the rows (right-orthonormal site tensor)
+      for (int r = 0; r < rows; ++r) {
+        for (int q = 0; q < r; ++q) {
+          double dp = 0;
+          for (int j = 0; j < cols; ++j) dp += B[(long)r * cols + j] * B[(long)q * cols + j];
+          for (int j = 0; j < cols; ++j) B[(long)r * cols + j] -= dp * B[(long)q * cols + j];
+        }
+        double nr = 0;
+        for (int j = 0; j < cols; ++j) nr += B[(long)r * cols + j] * B[(long)r * cols + j];
+        nr = std::sqrt(nr);
+        for (int j = 0; j < cols; ++j) B[(long)r * cols + j] = nr > 1e-12 ? B[(long)r * cols + j] / nr : 0.0;
+      }
+    }
+    DBuf d;
+    d.alloc(&c, host.size() * sizeof(double));
+    cuda_check(cudaMemcpyAsync(d.p, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c.s()),
+               "upload mps");
+    cuda_check(cudaStreamSynchronize(c.s()), "upload mps sync");
+    set_site_rf(c, m, p, std::move(d));
+  }
+  m.present = true;
+}
+
+// ---------------------------------------------------------------------------
+double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
+  int k = c.k;
+  init_random_mps(c, c.phi0, std::min(M0, 16), true, c.opts.seed);
+  bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
+  double E = 0;
+  bool all_conv = true;
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    for (int dir = 0; dir < 2; ++dir) {
+      bool right = dir == 0;
+      for (int step = 0; step <= k - 2; ++step) {
+        int l = right ? step : k - 2 - step;
+        SigmaPlan P;
+        make_sigma_plan(c, c.f00, l, P);
+        long n = P.nk;
+        DBuf x, dg;
+        x.alloc(&c, std::max(n, 1L) * sizeof(double));
+        dg.alloc(&c, std::max(n, 1L) * sizeof(double));
+        form_two_site(c, c.phi0, l, x.d());
+        sigma_diag(c, P, dg.d());
+        bool conv = false;
+        E = davidson(c, P, x.d(), n, dg.d(), std::max(c.opts.tol, 1e-13), c.opts.max_iter,
+                     c.opts.davidson_max_subspace, &conv);
+        all_conv &= conv;
+        double disc = truncate(c, c.phi0, l, x.d(), M0, right);
+        c.max_disc = std::max(c.max_disc, disc);
+        invalidate_site(c.f00, l);
+        invalidate_site(c.f00, l + 1);
+        if (right) env_update_left(c, c.f00, l, P.lf);
+        else env_update_right(c, c.f00, l + 1, P.rf);
+        if (c.opts.verbose)
+          fprintf(stderr, "[dmrg] sweep %d %s l=%d n=%ld E=%.12f disc=%.2e\n", sw, right ? "R" : "L", l, n, E, disc);
+      }
+    }
+  }
+  c.E0 = E;
+  c.have_E0 = true;
+  if (!all_conv && c.opts.verbose) fprintf(stderr, "[dmrg] warning: some Davidson solves hit max_iter\n");
+  return E;
+}
+
+double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
+  int k = c.k;
+  MPSLCC_REQUIRE(c.phi0.present && c.have_E0, ST_STATE, "lcc_sweep needs a reference (dmrg_reference)");
+  if (!c.phi1.present) {
+    init_random_mps(c, c.phi1, std::min(M1, 16), false, c.opts.seed + 1);
+    bind(c, c.f11, &c.phi1, MPO_H0, &c.phi1);
+    bind(c, c.f10, &c.phi1, MPO_H, &c.phi0);
+    bind(c, c.s10, &c.phi1, MPO_ID, &c.phi0);
+  }
+  c.e3_valid = false;
+  c.u11.L.clear();
+  c.h11.L.clear();
+  int prec = c.opts.prec;
+  double J = 0, E2 = 0;
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    double s_sig0 = c.st.sigma_seconds, f_sig0 = c.st.sigma_flops;
+    long long n_sig0 = c.st.sigma_calls, n_k0 = c.st.kernel_launches;
+    cudaEventRecord(t0, c.s());
+    for (int dir = 0; dir < 2; ++dir) {
+      bool right = dir == 0;
+      for (int step = 0; step <= k - 2; ++step) {
+        int l = right ? step : k - 2 - step;
+        SigmaPlan P11, P10, PS;
+        make_sigma_plan(c, c.f11, l, P11);
+        make_sigma_plan(c, c.f10, l, P10);
+        make_sigma_plan(c, c.s10, l, PS);
+        long n = P11.nk, n0 = P10.nk;
+        DBuf xb, bb, ub, vb, sb, dg, p0;
+        xb.alloc(&c, std::max(n, 1L) * sizeof(double));
+        bb.alloc(&c, std::max(n, 1L) * sizeof(double));
+        ub.alloc(&c, std::max(n, 1L) * sizeof(double));
+        sb.alloc(&c, std::max(n, 1L) * sizeof(double));
+        dg.alloc(&c, std::max(n, 1L) * sizeof(double));
+        p0.alloc(&c, std::max(n0, 1L) * sizeof(double));
+        form_two_site(c, c.phi0, l, p0.d());
+        sigma_apply(c, P10, p0.d(), sb.d(), MPSLCC_FP64);   // P1^T H Phi0
+        sigma_apply(c, PS, p0.d(), ub.d(), MPSLCC_FP64);    // v = P1^T Phi0
+        // b = -(P1^T H Phi0 - E0 v), then project out v
+        copyv(c, bb.d(), ub.d(), n);
+        launch_axpby(n, -1.0, sb.d(), c.E0, bb.d(), c.s());
+        double vn = std::sqrt(std::max(0.0, dev_dot(c, ub.d(), ub.d(), n)));
+        const double* u = nullptr;
+        if (vn > 1e-10) {
+          launch_scale(n, 1.0 / vn, ub.d(), c.s());
+          u = ub.d();
+        }
+        project(c, u, bb.d(), n);
+        form_two_site(c, c.phi1, l, xb.d());
+        sigma_diag(c, P11, dg.d());
+        LinOp A{&P11, c.E0, u, Vec()};
+        int its = 0;
+        bool indef = false;
+        double bn = std::sqrt(std::max(0.0, dev_dot(c, bb.d(), bb.d(), n)));
+        if (prec == MPSLCC_FP64) {
+          solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(c.opts.tol, 1e-14), c.opts.max_iter, MPSLCC_FP64,
+                       &its, &indef);
+        } else {
+          // mixed precision: inner solves with tensor-core sigma products,
+          // FP64 residuals r = b - A x as outer iterative refinement
+          Vec r, dx, ax;
+          r.alloc(c, n);
+          dx.alloc(c, n);
+          ax.alloc(c, n);
+          for (int ref = 0; ref < std::max(1, c.opts.refine_steps); ++ref) {
+            A.apply(c, xb.d(), ax.d(), MPSLCC_FP64);
+            copyv(c, r.d(), bb.d(), n);
+            launch_axpy(n, -1.0, ax.d(), r.d(), c.s());
+            double rn = vnorm(c, r);
+            if (rn <= std::max(c.opts.tol, 1e-14) * bn) break;
+            launch_fill(n, 0.0, dx.d(), c.s());
+            int it2 = 0;
+            solve_linear(c, A, r.d(), dx.d(), dg.d(), n, 1e-3, c.opts.max_iter, prec, &it2, &indef);
+            its += it2;
+            launch_axpy(n, 1.0, dx.d(), xb.d(), c.s());
+          }
+        }
+        // Hylleraas value J = x.Ax - 2 x.b (FP64)
+        Vec ax;
+        ax.alloc(c, n);
+        A.apply(c, xb.d(), ax.d(), MPSLCC_FP64);
+        J = dev_dot(c, xb.d(), ax.d(), n) - 2.0 * dev_dot(c, xb.d(), bb.d(), n);
+        E2 = J;
+        double disc = truncate(c, c.phi1, l, xb.d(), M1, right);
+        c.max_disc = std::max(c.max_disc, disc);
+        for (Family* F : {&c.f11, &c.f10, &c.s10}) {
+          invalidate_site(*F, l);
+          invalidate_site(*F, l + 1);
+        }
+        if (right) {
+          env_update_left(c, c.f11, l, P11.lf);
+          env_update_left(c, c.f10, l, P10.lf);
+          env_update_left(c, c.s10, l, PS.lf);
+        } else {
+          env_update_right(c, c.f11, l + 1, P11.rf);
+          env_update_right(c, c.f10, l + 1, P10.rf);
+          env_update_right(c, c.s10, l + 1, PS.rf);
+        }
+        if (c.opts.verbose)
+          fprintf(stderr, "[lcc] sweep %d %s l=%d n=%ld its=%d%s J=%.12f disc=%.2e\n", sw, right ? "R" : "L", l, n,
+                  its, indef ? " (minres)" : "", J, disc);
+      }
+    }
+    cudaEventRecord(t1, c.s());
+    cudaEventSynchronize(t1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, t0, t1);
+    c.st.last_sweep_seconds = ms * 1e-3;
+    c.st.last_sweep_sigma_seconds = c.st.sigma_seconds - s_sig0;
+    c.st.last_sweep_sigma_flops = c.st.sigma_flops - f_sig0;
+    c.st.last_sweep_sigma_calls = c.st.sigma_calls - n_sig0;
+    c.st.last_sweep_kernel_launches = c.st.kernel_launches - n_k0;
+    c.sweeps_done++;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  c.J = J;
+  c.E2 = E2;
+  c.have_E2 = true;
+  // overlap and norm at position 0 (Phi1's centre after the left pass)
+  {
+    SigmaPlan PS;
+    make_sigma_plan(c, c.s10, 0, PS);
+    DBuf x, p0, v;
+    x.alloc(&c, std::max(PS.nb, 1L) * sizeof(double));
+    v.alloc(&c, std::max(PS.nb, 1L) * sizeof(double));
+    p0.alloc(&c, std::max(PS.nk, 1L) * sizeof(double));
+    form_two_site(c, c.phi1, 0, x.d());
+    form_two_site(c, c.phi0, 0, p0.d());
+    sigma_apply(c, PS, p0.d(), v.d(), MPSLCC_FP64);
+    c.ovl01 = dev_dot(c, x.d(), v.d(), PS.nb);
+    c.norm1 = dev_dot(c, x.d(), x.d(), PS.nb);
+  }
+  return E2;
+}
+
+void compute_e3(Ctx& c) {
+  MPSLCC_REQUIRE(c.phi1.present, ST_STATE, "E3 needs the first-order state");
+  bind(c, c.u11, &c.phi1, MPO_U, &c.phi1);
+  SigmaPlan P;
+  make_sigma_plan(c, c.u11, 0, P);
+  DBuf x, y;
+  x.alloc(&c, std::max(P.nb, 1L) * sizeof(double));
+  y.alloc(&c, std::max(P.nb, 1L) * sizeof(double));
+  form_two_site(c, c.phi1, 0, x.d());
+  sigma_apply(c, P, x.d(), y.d(), MPSLCC_FP64);
+  c.E3 = dev_dot(c, x.d(), y.d(), P.nb);
+  c.e3_valid = true;
+  c.u11.L.clear();
+  c.u11.R.clear();
+}
+
+}  // namespace mpslcc
