@@ -682,17 +682,20 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P) {
     base_tiles += (long long)((dFLb + 63) / 64) * ((dFRb + 63) / 64);
   }
   const long long target = 152LL * 6;
-  P.split2 = false;
+  P.zero_y = false;
   for (size_t bi = 0; bi < P.mid_b.size(); ++bi) {
     long K = lf.K[bi];
     int dFLb = lf.FLb.d[lf.kb[bi]], dFRb = rf.FRb.d[rf.kb[bi]];
-    if (K == 0) continue;
+    if (K == 0) {  // no operator channel reaches this output sector: it stays zero
+      P.zero_y = true;
+      continue;
+    }
     GemmTask t = gemm(lf.data.d() + lf.off[bi], P.tt.d() + P.tt_off[bi], P.yout.d() + P.off_b[bi], dFLb, dFRb, (int)K,
                       (int)K, (int)K, dFRb, GEMM_TB);
     if (base_tiles < target) {
       long long f = (target + base_tiles - 1) / std::max(1LL, base_tiles);
       t.ksplit = (int)std::max(1LL, std::min(f, (long long)(K / 256)));
-      if (t.ksplit > 1) P.split2 = true;
+      if (t.ksplit > 1) P.zero_y = true;
     }
     t2.push_back(t);
     fl += 2.0 * (double)dFLb * dFRb * K;
@@ -704,7 +707,6 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P) {
   P.n2 = (int)t2.size();
   P.tiles1 = t1.empty() ? 0 : plan_gemm_tiles(t1.data(), P.n1);
   P.tiles2 = t2.empty() ? 0 : plan_gemm_tiles(t2.data(), P.n2);
-  if (P.split2 && !t2.empty()) P.split2 = true;
   P.tasks1.release();
   P.tasks2.release();
   P.tasks1.alloc(&c, std::max<size_t>(t1.size(), 1) * sizeof(GemmTask));
@@ -725,7 +727,7 @@ void sigma_apply(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
   }
   if (P.nk > 0)
     cuda_check(cudaMemcpyAsync(P.xin.p, x, P.nk * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma in");
-  if (P.split2 || P.n2 == 0)
+  if (P.zero_y || P.n2 == 0)
     cuda_check(cudaMemsetAsync(P.yout.p, 0, std::max(P.nb, 1L) * sizeof(double), c.s()), "sigma zero");
   launch_gemm_f64((const GemmTask*)P.tasks1.p, P.n1, P.tiles1, c.s());
   launch_gemm_f64((const GemmTask*)P.tasks2.p, P.n2, P.tiles2, c.s());

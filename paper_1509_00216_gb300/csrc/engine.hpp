@@ -156,7 +156,7 @@ struct SigmaPlan {
   DBuf tasks1, tasks2;
   int n1 = 0, n2 = 0;
   long long tiles1 = 0, tiles2 = 0;
-  bool split2 = false;
+  bool zero_y = false;
   double flops = 0.0;                  // algorithmic flops of one application
   // mixed precision copies (tensor-core path)
   int lowp = -1;                       // prec of the low-precision copies

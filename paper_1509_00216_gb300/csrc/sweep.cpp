@@ -219,12 +219,15 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
   z.alloc(c, n);
   p.alloc(c, n);
   Ap.alloc(c, n);
+  const double atol = 1e-14;
   double bn = std::sqrt(std::max(0.0, dev_dot(c, b, b, n)));
-  if (bn < 1e-300) {
+  if (bn <= atol) {  // right-hand side vanishes to working precision
     launch_fill(n, 0.0, x, c.s());
     *iters = 0;
-    return 0.0;
+    *indefinite = false;
+    return bn;
   }
+  const double thr = std::max(tol * bn, atol);
   project(c, A.u, x, n);
   A.apply(c, x, Ap.d(), prec);
   copyv(c, r.d(), b, n);
@@ -239,11 +242,11 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
   double rn = vnorm(c, r);
   int it = 0;
   *indefinite = false;
-  while (rn > tol * bn && it < maxit) {
+  while (rn > thr && it < maxit) {
     A.apply(c, p.d(), Ap.d(), prec);
     double pAp = dev_dot(c, p.d(), Ap.d(), n);
-    if (pAp <= 0) {
-      *indefinite = true;
+    if (!(pAp > 0)) {
+      *indefinite = std::isfinite(pAp);
       break;
     }
     double alpha = rz / pAp;
@@ -270,7 +273,7 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
     double gam0 = 1, gam1 = 1, sig0 = 0, sig1 = 0, betaold = 0;
     if (beta > 0) launch_scale(n, 1.0 / beta, v1.d(), c.s());
     rn = beta;
-    while (rn > tol * bn && it < maxit && beta > 1e-300) {
+    while (rn > thr && it < maxit && beta > 1e-300) {
       A.apply(c, v1.d(), av.d(), prec);
       double alpha = dev_dot(c, v1.d(), av.d(), n);
       launch_axpy(n, -alpha, v1.d(), av.d(), c.s());
