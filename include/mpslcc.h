@@ -55,7 +55,10 @@ typedef enum {
   MPSLCC_E_INTERNAL = 7
 } mpslcc_status;
 
-typedef enum { MPSLCC_FP64 = 0, MPSLCC_TF32 = 1, MPSLCC_BF16 = 2 } mpslcc_prec;
+/* FP64 DFMA; TF32 or BF16 tensor-core operands (FP32 accumulation); BF16X3:
+   operands split into BF16 hi + lo parts, hi*hi + hi*lo + lo*hi accumulated
+   in FP32 (about 2^-16 relative accuracy) */
+typedef enum { MPSLCC_FP64 = 0, MPSLCC_TF32 = 1, MPSLCC_BF16 = 2, MPSLCC_BF16X3 = 3 } mpslcc_prec;
 
 /* Operators for mpslcc_apply_heff / mpslcc_local_dim. */
 typedef enum {
@@ -114,6 +117,13 @@ typedef struct {
   long long last_sweep_kernel_launches;
   int max_bond_dim;
   int mpo_max_bond;         /* largest MPO bond dimension (H)                */
+  double tc_phase1_seconds; /* device time of tensor-core sigma phase 1      */
+  double tc_phase2_seconds; /* ... and phase 2                              */
+  double tc_phase1_bytes;   /* algorithmic operand + result bytes, phase 1   */
+  double tc_phase2_bytes;   /* ... phase 2                                   */
+  double f64_phase1_seconds;/* device time of the FP64 sigma phases          */
+  double f64_phase2_seconds;
+  long long tc_launches;
 } mpslcc_stats;
 
 /* Fill *opts with defaults (device 0, FP64, tol 1e-10, max_iter 200, auto
@@ -202,6 +212,15 @@ mpslcc_status mpslcc_export_mps(mpslcc_ctx* ctx, int which, int* meta, long* n_i
 mpslcc_status mpslcc_mpo_bond_dims(mpslcc_ctx* ctx, int which, int* bond_dims);
 mpslcc_status mpslcc_export_mpo_site(mpslcc_ctx* ctx, int which, int site, int* idx,
                                      double* val, long* count);
+
+/* Diagnostic entry point: C = A B^T through the tensor-core GEMM kernel of
+   the sigma path (one task; A m x k and B n x k row-major FP64 host arrays,
+   rounded to prec = TF32 or BF16; C m x n FP64 host output).  mode 0 adds
+   FP32 partial sums over `ksplit` K chunks atomically, 1 stores BF16, 2
+   stores FP32.  There is no counterpart in the paper; it exists to test the
+   kernel in isolation. */
+mpslcc_status mpslcc_debug_tc_gemm(mpslcc_ctx* ctx, int prec, int m, int n, int k, const double* A,
+                                   const double* B, double* C, int mode, int ksplit);
 
 mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out);
 mpslcc_status mpslcc_reset_stats(mpslcc_ctx* ctx);

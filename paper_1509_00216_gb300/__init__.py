@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmpslcc.so")
 
-FP64, TF32, BF16 = 0, 1, 2
+FP64, TF32, BF16, BF16X3 = 0, 1, 2, 3
 OP_H0_11, OP_H0_00, OP_H_10, OP_U_11, OP_S_10, OP_H_11 = range(6)
 MPO_H, MPO_H0, MPO_U, MPO_ID = range(4)
 
@@ -28,6 +28,7 @@ EXPORTED = [
     "mpslcc_set_spaces", "mpslcc_dmrg_reference", "mpslcc_lcc_sweep", "mpslcc_energy", "mpslcc_local_dim",
     "mpslcc_apply_heff", "mpslcc_apply_heff_device", "mpslcc_load_mps", "mpslcc_export_mps",
     "mpslcc_mpo_bond_dims", "mpslcc_export_mpo_site", "mpslcc_get_stats", "mpslcc_reset_stats",
+    "mpslcc_debug_tc_gemm",
 ]
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -53,7 +54,10 @@ class Stats(C.Structure):
                 ("last_sweep_seconds", C.c_double), ("last_sweep_sigma_seconds", C.c_double),
                 ("last_sweep_sigma_flops", C.c_double), ("last_sweep_sigma_calls", C.c_longlong),
                 ("last_sweep_kernel_launches", C.c_longlong), ("max_bond_dim", C.c_int),
-                ("mpo_max_bond", C.c_int)]
+                ("mpo_max_bond", C.c_int), ("tc_phase1_seconds", C.c_double), ("tc_phase2_seconds", C.c_double),
+                ("tc_phase1_bytes", C.c_double), ("tc_phase2_bytes", C.c_double),
+                ("f64_phase1_seconds", C.c_double), ("f64_phase2_seconds", C.c_double),
+                ("tc_launches", C.c_longlong)]
 
 
 def _load():
@@ -83,6 +87,7 @@ def _load():
         "mpslcc_export_mpo_site": (C.c_int, [vp, C.c_int, C.c_int, ip, dp, lp]),
         "mpslcc_get_stats": (C.c_int, [vp, C.POINTER(Stats)]),
         "mpslcc_reset_stats": (C.c_int, [vp]),
+        "mpslcc_debug_tc_gemm": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -287,6 +292,15 @@ class Context:
         s = Stats()
         self._check(lib().mpslcc_get_stats(self.h, C.byref(s)))
         return {f: getattr(s, f) for f, _ in Stats._fields_}
+
+    def debug_tc_gemm(self, A, B, prec=BF16, mode=0, ksplit=1):
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        m, k = A.shape
+        n = B.shape[0]
+        C_ = np.zeros((m, n))
+        self._check(lib().mpslcc_debug_tc_gemm(self.h, prec, m, n, k, _dptr(A), _dptr(B), _dptr(C_), mode, ksplit))
+        return C_
 
     def reset_stats(self):
         self._check(lib().mpslcc_reset_stats(self.h))

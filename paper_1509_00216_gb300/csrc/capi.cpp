@@ -118,8 +118,7 @@ mpslcc_status mpslcc_create(mpslcc_ctx** out, const mpslcc_opts* opts) {
     }
     MPSLCC_REQUIRE(cusolverDnCreate(&c.solver) == CUSOLVER_STATUS_SUCCESS, ST_CUDA, "cusolverDnCreate failed");
     cusolverDnSetStream(c.solver, c.stream);
-    cuda_check(cudaEventCreate(&c.ev0), "event");
-    cuda_check(cudaEventCreate(&c.ev1), "event");
+    for (cudaEvent_t* e : {&c.ev0, &c.ev1, &c.ev_p0, &c.ev_p1, &c.ev_p2}) cuda_check(cudaEventCreate(e), "event");
   });
   if (st != MPSLCC_OK) {
     delete ctx;
@@ -143,8 +142,8 @@ mpslcc_status mpslcc_destroy(mpslcc_ctx* ctx) {
       b->release();
     cudaStreamSynchronize(c.stream);
     if (c.solver) cusolverDnDestroy(c.solver);
-    if (c.ev0) cudaEventDestroy(c.ev0);
-    if (c.ev1) cudaEventDestroy(c.ev1);
+    for (cudaEvent_t e : {c.ev0, c.ev1, c.ev_p0, c.ev_p1, c.ev_p2})
+      if (e) cudaEventDestroy(e);
     if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
   }
   delete ctx;
@@ -286,7 +285,7 @@ static void apply_heff_dev(Ctx& c, int site, int op, const double* d_psi, double
   need_device(c);
   cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
   MPSLCC_REQUIRE(site >= 0 && site <= c.k - 2, ST_ARG, "site out of range");
-  MPSLCC_REQUIRE(prec >= 0 && prec <= 2, ST_ARG, "bad precision");
+  MPSLCC_REQUIRE(prec >= 0 && prec <= 3, ST_ARG, "bad precision");
   Family& F = family_for(c, op);
   SigmaPlan P;
   make_sigma_plan(c, F, site, P);
@@ -509,6 +508,25 @@ mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out) {
     out->last_sweep_kernel_launches = c.st.last_sweep_kernel_launches;
     out->max_bond_dim = c.st.max_bond_dim;
     out->mpo_max_bond = c.have_mpo ? c.mpo[MPO_H].max_bond() : 0;
+    out->tc_phase1_seconds = c.st.tc_phase1_s;
+    out->tc_phase2_seconds = c.st.tc_phase2_s;
+    out->tc_phase1_bytes = c.st.tc_phase1_bytes;
+    out->tc_phase2_bytes = c.st.tc_phase2_bytes;
+    out->f64_phase1_seconds = c.st.f64_phase1_s;
+    out->f64_phase2_seconds = c.st.f64_phase2_s;
+    out->tc_launches = c.st.tc_launches;
+  });
+}
+
+mpslcc_status mpslcc_debug_tc_gemm(mpslcc_ctx* ctx, int prec, int m, int n, int k, const double* A,
+                                   const double* B, double* C, int mode, int ksplit) {
+  return guard(ctx, [&](Ctx& c) {
+    need_device(c);
+    MPSLCC_REQUIRE(prec >= MPSLCC_TF32 && prec <= MPSLCC_BF16X3, ST_ARG, "prec must be TF32, BF16 or BF16X3");
+    MPSLCC_REQUIRE(!(prec == MPSLCC_BF16X3 && (mode == 1 || mode == 3)), ST_ARG, "split operands need an FP32 output mode");
+    MPSLCC_REQUIRE(m >= 1 && n >= 1 && k >= 1 && A && B && C && mode >= 0 && mode <= 2, ST_ARG, "bad argument");
+    cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
+    tc_selftest(c, prec, m, n, k, A, B, C, mode, std::max(1, ksplit));
   });
 }
 

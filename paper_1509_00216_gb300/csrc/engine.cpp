@@ -56,6 +56,18 @@ void Ctx::check_range(const void* ptr, long long first, long long last, const ch
   if (!ok) throw Error(ST_INTERNAL, std::string("device access out of bounds in ") + what);
 }
 
+void Ctx::check_bytes(const void* ptr, long long nbytes, const char* what) const {
+  if (nbytes <= 0) return;
+  uintptr_t a = (uintptr_t)ptr, b = a + (uintptr_t)nbytes;
+  auto it = allocs.upper_bound(a);
+  bool ok = false;
+  if (it != allocs.begin()) {
+    --it;
+    ok = a >= it->first && b <= it->first + it->second;
+  }
+  if (!ok) throw Error(ST_INTERNAL, std::string("device access out of bounds in ") + what);
+}
+
 void DBuf::release() {
   if (p && c) c->allocs.erase((uintptr_t)p);
   if (p && c) {
@@ -645,7 +657,6 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P) {
   ensure_envs(c, F, l);
   P.l = l;
   P.fam = &F;
-  P.lowp = -1;
   two_site_middle(*F.bra, l, P.mid_b, P.off_b, P.nb);
   two_site_middle(*F.ket, l, P.mid_k, P.off_k, P.nk);
   make_left_fused(c, F, l, P.mid_b, P.mid_k, P.lf);
@@ -722,15 +733,18 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P) {
 
 void sigma_apply(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
   if (prec != MPSLCC_FP64) {
-    tc_sigma(c, P, x, y);
+    tc_sigma(c, P, x, y, prec);
     return;
   }
   if (P.nk > 0)
     cuda_check(cudaMemcpyAsync(P.xin.p, x, P.nk * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma in");
   if (P.zero_y || P.n2 == 0)
     cuda_check(cudaMemsetAsync(P.yout.p, 0, std::max(P.nb, 1L) * sizeof(double), c.s()), "sigma zero");
+  cudaEventRecord(c.ev_p0, c.s());
   launch_gemm_f64((const GemmTask*)P.tasks1.p, P.n1, P.tiles1, c.s());
+  cudaEventRecord(c.ev_p1, c.s());
   launch_gemm_f64((const GemmTask*)P.tasks2.p, P.n2, P.tiles2, c.s());
+  cudaEventRecord(c.ev_p2, c.s());
   cuda_check(cudaGetLastError(), "sigma launch");
   if (P.nb > 0)
     cuda_check(cudaMemcpyAsync(y, P.yout.p, P.nb * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma out");
@@ -738,6 +752,12 @@ void sigma_apply(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
   c.st.gemm_launches += 2;
   c.st.sigma_calls++;
   c.st.sigma_flops += P.flops;
+  cuda_check(cudaEventSynchronize(c.ev_p2), "sigma phase sync");
+  float m1 = 0, m2 = 0;
+  cudaEventElapsedTime(&m1, c.ev_p0, c.ev_p1);
+  cudaEventElapsedTime(&m2, c.ev_p1, c.ev_p2);
+  c.st.f64_phase1_s += m1 * 1e-3;
+  c.st.f64_phase2_s += m2 * 1e-3;
 }
 
 void sigma_diag(Ctx& c, SigmaPlan& P, double* diag) {

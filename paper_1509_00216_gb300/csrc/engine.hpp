@@ -158,12 +158,12 @@ struct SigmaPlan {
   long long tiles1 = 0, tiles2 = 0;
   bool zero_y = false;
   double flops = 0.0;                  // algorithmic flops of one application
-  // mixed precision copies (tensor-core path)
-  int lowp = -1;                       // prec of the low-precision copies
-  DBuf lcat_lp, rstk_lp, tt_lp, x_lp;  // operand copies
-  DBuf tc_tasks1, tc_tasks2;
-  int tc_n1 = 0, tc_n2 = 0;
-  long long tc_tiles1 = 0, tc_tiles2 = 0;
+  // low-precision operand copies and task lists of the tensor-core path
+  struct TcState* tc = nullptr;
+  SigmaPlan() = default;
+  SigmaPlan(const SigmaPlan&) = delete;
+  SigmaPlan& operator=(const SigmaPlan&) = delete;
+  ~SigmaPlan();
 };
 
 struct Stats {
@@ -172,6 +172,10 @@ struct Stats {
   double last_sweep_seconds = 0, last_sweep_sigma_seconds = 0, last_sweep_sigma_flops = 0;
   long long last_sweep_sigma_calls = 0, last_sweep_kernel_launches = 0;
   int max_bond_dim = 0;
+  // per-phase device time / algorithmic bytes of the sigma kernels
+  double tc_phase1_s = 0, tc_phase2_s = 0, tc_phase1_bytes = 0, tc_phase2_bytes = 0;
+  double f64_phase1_s = 0, f64_phase2_s = 0;
+  long long tc_launches = 0;
 };
 
 struct Ctx {
@@ -179,6 +183,7 @@ struct Ctx {
   // address range on the host before a launch
   std::map<uintptr_t, size_t> allocs;
   void check_range(const void* p, long long first, long long last, const char* what) const;
+  void check_bytes(const void* p, long long nbytes, const char* what) const;
 
   int device = 0;
   bool host_only = false;
@@ -187,7 +192,7 @@ struct Ctx {
   mpslcc_opts opts{};
   std::string err;
   cusolverDnHandle_t solver = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_p0 = nullptr, ev_p1 = nullptr, ev_p2 = nullptr;
 
   // problem
   int k = 0, n_elec = 0, two_sz = 0;
@@ -251,7 +256,9 @@ void ensure_envs(Ctx& c, Family& F, int l);
 
 // tensor-core path (tc_gemm.cu)
 void tc_prepare(Ctx& c, SigmaPlan& P, int prec);
-void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y);
+void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec);
+void tc_selftest(Ctx& c, int prec, int m, int n, int k, const double* A, const double* B, double* C, int mode,
+                 int ksplit);
 
 // sweeps (sweep.cpp)
 void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed);

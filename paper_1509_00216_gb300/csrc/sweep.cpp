@@ -694,33 +694,39 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
         int its = 0;
         bool indef = false;
         double bn = std::sqrt(std::max(0.0, dev_dot(c, bb.d(), bb.d(), n)));
-        if (prec == MPSLCC_FP64) {
-          solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(c.opts.tol, 1e-14), c.opts.max_iter, MPSLCC_FP64,
-                       &its, &indef);
+        if (prec == MPSLCC_FP64 || prec == MPSLCC_BF16X3) {
+          // one precision throughout (BF16X3: split-BF16 products, ~2^-16)
+          solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(c.opts.tol, 1e-14), c.opts.max_iter, prec, &its,
+                       &indef);
         } else {
-          // mixed precision: inner solves with tensor-core sigma products,
-          // FP64 residuals r = b - A x as outer iterative refinement
+          // iterative refinement: inner solves with plain TF32 / BF16 sigma
+          // products, residuals r = b - A x with split-BF16 products and
+          // FP64 vectors
           Vec r, dx, ax;
           r.alloc(c, n);
           dx.alloc(c, n);
           ax.alloc(c, n);
           for (int ref = 0; ref < std::max(1, c.opts.refine_steps); ++ref) {
-            A.apply(c, xb.d(), ax.d(), MPSLCC_FP64);
+            A.apply(c, xb.d(), ax.d(), MPSLCC_BF16X3);
             copyv(c, r.d(), bb.d(), n);
             launch_axpy(n, -1.0, ax.d(), r.d(), c.s());
             double rn = vnorm(c, r);
             if (rn <= std::max(c.opts.tol, 1e-14) * bn) break;
             launch_fill(n, 0.0, dx.d(), c.s());
             int it2 = 0;
-            solve_linear(c, A, r.d(), dx.d(), dg.d(), n, 1e-3, c.opts.max_iter, prec, &it2, &indef);
+            solve_linear(c, A, r.d(), dx.d(), dg.d(), n, 0.05, c.opts.max_iter, prec, &it2, &indef);
             its += it2;
             launch_axpy(n, 1.0, dx.d(), xb.d(), c.s());
           }
         }
-        // Hylleraas value J = x.Ax - 2 x.b (FP64)
+        // Hylleraas value J = x.Ax - 2 x.b; with FP64 products at the last
+        // position of the sweep (the reported E2), otherwise in the solve's
+        // residual precision
         Vec ax;
         ax.alloc(c, n);
-        A.apply(c, xb.d(), ax.d(), MPSLCC_FP64);
+        const bool last = (sw == n_sweeps - 1) && !right && l == 0;
+        const int jprec = (prec == MPSLCC_FP64 || last) ? MPSLCC_FP64 : MPSLCC_BF16X3;
+        A.apply(c, xb.d(), ax.d(), jprec);
         J = dev_dot(c, xb.d(), ax.d(), n) - 2.0 * dev_dot(c, xb.d(), bb.d(), n);
         E2 = J;
         double disc = truncate(c, c.phi1, l, xb.d(), M1, right);

@@ -1,13 +1,755 @@
-// Tensor-core (tcgen05) sigma path.
+// Tensor-core sigma path for sm_103a: a grouped GEMM whose operand tiles are
+// staged by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage
+// shared-memory ring and multiplied by tcgen05.mma (kind::f16 with BF16
+// operands, or kind::tf32) into an FP32 accumulator in tensor memory.  One
+// thread issues TMA, one thread issues MMA, and the four warps of the CTA
+// drain the accumulator with tcgen05.ld.
+//
+// Each task carries its own tensor maps, so the uneven quantum-number
+// sectors of one sigma product (every operator class, every middle sector)
+// run in one launch per phase.  The epilogue either stores rows with a
+// batched row remap (phase 1 writes the stacked T_w^T blocks) or adds FP32
+// partial sums atomically (phase 2, split over the channel dimension K).
+// Every mbarrier wait is bounded; on expiry the kernel records an error flag,
+// stops issuing work, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
 #include "engine.hpp"
 
 namespace mpslcc {
 
-void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
-  throw Error(ST_ARG, "tensor-core sigma path not built yet");
+struct alignas(64) TcTask {
+  CUtensorMap ma;       // A: rows x K, K contiguous
+  CUtensorMap mb;       // B: rows x K, K contiguous
+  void* C;
+  long long bstride;    // output offset between row batches (elements)
+  int rpb;              // rows per batch of the output remap
+  int ldc;
+  int m, n, k;
+  int ksteps, kchunk, ksplit;
+  int ntile;            // UMMA N (multiple of 16, <= 256)
+  int tm, tn;
+  int mode;             // 0: FP32 atomic add, 1: BF16 store, 2: FP32 store,
+                        // 3: split BF16 store (hi at +0, lo at +soff, hi at +2 soff)
+  long long soff;
+  long long tile0;
+};
+
+namespace {
+
+constexpr int STAGES = 4;
+constexpr int A_BYTES = 128 * 128;           // 128 rows x 128 bytes
+constexpr int B_BYTES_MAX = 256 * 128;       // up to 256 rows x 128 bytes
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES_MAX;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on every mbarrier wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y) {
-  throw Error(ST_ARG, "tensor-core sigma path not built yet");
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; on expiry sets *err and returns false
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (gtimer() - t0 > WAIT_NS) break;
+    __nanosleep(32);
+  }
+  atomicExch(err, code);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t sdesc(const void* p) {
+  // K-major operand tile, 128-byte swizzle: 8-row groups of 1024 bytes
+  uint64_t a = smem_u32(p);
+  uint64_t d = (a >> 4) & 0x3FFFull;
+  d |= 1ull << 16;                    // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= 1ull << 46;                    // descriptor version
+  d |= 2ull << 61;                    // SWIZZLE_128B
+  return d;
+}
+
+template <int PREC>
+__device__ __forceinline__ uint32_t idesc(int M, int N) {
+  uint32_t f = PREC == MPSLCC_BF16 ? 1u : 2u;  // BF16 or TF32 operands
+  uint32_t d = 1u << 4;                        // FP32 accumulator
+  d |= f << 7;
+  d |= f << 10;
+  d |= (uint32_t)(N >> 3) << 17;
+  d |= (uint32_t)(M >> 4) << 24;
+  return d;
+}
+
+template <int PREC>
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if (PREC == MPSLCC_BF16)
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int find_tc(const TcTask* t, int n, long long tile) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (t[mid].tile0 <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
+                                                          long long total, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  volatile uint32_t* tslot = (volatile uint32_t*)(done + 1);
+  volatile int* s_abort = (volatile int*)(tslot + 1);
+  constexpr int KT = PREC == MPSLCC_BF16 ? 64 : 32;  // K elements per 128-byte row
+  const int warp = threadIdx.x >> 5;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32((const void*)tslot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tslot;
+
+  uint32_t it = 0, tcount = 0;
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
+    if (*s_abort) break;
+    const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
+    const long long local = tile - T->tile0;
+    const int tiles_mn = T->tm * T->tn;
+    const int ks = (int)(local / tiles_mn);
+    const int r = (int)(local - (long long)ks * tiles_mn);
+    const int tmi = r / T->tn, tni = r - (r / T->tn) * T->tn;
+    const int kt0 = ks * T->kchunk;
+    const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
+    const int row0 = tmi * 128, col0 = tni * T->ntile;
+    const int ntile = T->ntile;
+    if (threadIdx.x == 0) {
+      // TMA producer
+      const uint32_t bbytes = (uint32_t)ntile * 128u;
+      for (int j = 0; j < nk; ++j) {
+        const uint32_t s = (it + j) % STAGES, ph = ((it + j) / STAGES) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, err, 1)) { *s_abort = 1; break; }
+        mbar_expect_tx(&full[s], A_BYTES + bbytes);
+        tma_load_2d(smem + s * STAGE_BYTES, &T->ma, &full[s], (kt0 + j) * KT, row0);
+        tma_load_2d(smem + s * STAGE_BYTES + A_BYTES, &T->mb, &full[s], (kt0 + j) * KT, col0);
+      }
+    } else if (threadIdx.x == 32) {
+      // MMA issuer
+      const uint32_t id = idesc<PREC>(128, ntile);
+      for (int j = 0; j < nk; ++j) {
+        const uint32_t s = (it + j) % STAGES, ph = ((it + j) / STAGES) & 1u;
+        if (!mbar_wait(&full[s], ph, err, 2)) { *s_abort = 1; break; }
+        fence_after();
+        const uint64_t a = sdesc(smem + s * STAGE_BYTES);
+        const uint64_t b = sdesc(smem + s * STAGE_BYTES + A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) umma<PREC>(tmem, a + 2 * kk, b + 2 * kk, id, (j > 0 || kk > 0) ? 1u : 0u);
+        umma_commit(&empty[s]);
+      }
+      umma_commit(done);
+    }
+    it += nk;
+    // epilogue: thread t owns accumulator row t (tensor-memory lane t)
+    const bool ok = __syncthreads_and(mbar_wait(done, tcount & 1u, err, 3)) != 0;
+    fence_after();
+    if (ok && nk > 0) {
+      const int row = row0 + threadIdx.x;
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+      const bool live = row < T->m;
+      long long roff = 0;
+      if (live) roff = (long long)(row / T->rpb) * T->bstride + (long long)(row % T->rpb) * T->ldc;
+      for (int cb = 0; cb < ntile; cb += 32) {
+        uint32_t v[32];
+        tmem_ld32(taddr + cb, v);
+        if (!live) continue;
+        const int c0 = col0 + cb;
+        const int nv = min(32, T->n - c0);
+        if (nv <= 0) continue;
+        if (T->mode == 0) {
+          float* C = (float*)T->C + roff + c0;
+          for (int j = 0; j < nv; ++j) atomicAdd(C + j, __uint_as_float(v[j]));
+        } else if (T->mode == 1) {
+          __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
+          for (int j = 0; j < nv; ++j) C[j] = __float2bfloat16_rn(__uint_as_float(v[j]));
+        } else if (T->mode == 3) {
+          // two-term BF16 split of the FP32 result: [hi | lo | hi]
+          __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
+          for (int j = 0; j < nv; ++j) {
+            const float f = __uint_as_float(v[j]);
+            const __nv_bfloat16 h = __float2bfloat16_rn(f);
+            const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
+            C[j] = h;
+            C[j + T->soff] = l;
+            C[j + 2 * T->soff] = h;
+          }
+        } else {
+          float* C = (float*)T->C + roff + c0;
+          for (int j = 0; j < nv; ++j) C[j] = __uint_as_float(v[j]);
+        }
+      }
+    }
+    if (!ok) *s_abort = 1;
+    fence_before();
+    __syncthreads();
+  }
+  __syncthreads();
+  fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
+// window conversion FP64 -> BF16 / FP32 with batched strides
+struct ConvTask {
+  const double* src;
+  void* dst;
+  int rows, cols, src_ld, dst_ld, batch;
+  long long s_src, s_dst;
+  int pattern;          // 0 plain; split BF16 into three column blocks
+  long long soff;       // 1: [hi | hi | lo], 2: [hi | lo | hi] at offsets 0, soff, 2 soff
+  long long tile0;
+};
+constexpr int CONV_CHUNK = 4096;
+
+template <int PREC>
+__global__ void conv_kernel(const ConvTask* __restrict__ t, int ntasks, long long total) {
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (t[mid].tile0 <= tile) lo = mid;
+      else hi = mid - 1;
+    }
+    const ConvTask T = t[lo];
+    const long long local = tile - T.tile0;
+    const long long nel = (long long)T.rows * T.cols;
+    const long long per = (nel + CONV_CHUNK - 1) / CONV_CHUNK;
+    const int b = (int)(local / per);
+    const long long ch = local - (long long)b * per;
+    const long long e1 = min(nel, (ch + 1) * CONV_CHUNK);
+    for (long long e = ch * CONV_CHUNK + threadIdx.x; e < e1; e += blockDim.x) {
+      const int rr = (int)(e / T.cols), cc = (int)(e - (long long)rr * T.cols);
+      const double v = T.src[b * T.s_src + (long long)rr * T.src_ld + cc];
+      const long long o = b * T.s_dst + (long long)rr * T.dst_ld + cc;
+      if (PREC == MPSLCC_TF32) {
+        ((float*)T.dst)[o] = (float)v;
+      } else if (T.pattern == 0) {
+        ((__nv_bfloat16*)T.dst)[o] = __float2bfloat16_rn((float)v);
+      } else {
+        __nv_bfloat16* d = (__nv_bfloat16*)T.dst + o;
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
+        d[0] = h;
+        d[T.soff] = T.pattern == 1 ? h : l;
+        d[2 * T.soff] = T.pattern == 1 ? l : h;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cuda_check(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q), "driver entry point");
+    MPSLCC_REQUIRE(p && q == cudaDriverEntryPointSuccess, ST_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeFn)p;
+  }
+  return fn;
+}
+
+inline int esize(int prec) { return prec == MPSLCC_TF32 ? 4 : 2; }
+// kernel operand type: TF32, or BF16 (also for the split BF16x3 mode)
+inline int kprec(int prec) { return prec == MPSLCC_TF32 ? MPSLCC_TF32 : MPSLCC_BF16; }
+inline long pad8(long x) { return (x + 7) / 8 * 8; }
+
+// 2D K-major operand map: `rows` rows of `cols` logical elements, row pitch
+// `ld` elements; box = box_rows x 128 bytes, 128-byte swizzle.
+void encode_map(Ctx& c, CUtensorMap* map, int prec, const void* base, long rows, long cols, long ld, int box_rows) {
+  const int es = esize(prec);
+  MPSLCC_REQUIRE(((uintptr_t)base & 15) == 0, ST_INTERNAL, "tensor map base not 16-byte aligned");
+  MPSLCC_REQUIRE((ld * es) % 16 == 0, ST_INTERNAL, "tensor map pitch not a multiple of 16 bytes");
+  MPSLCC_REQUIRE(rows >= 1 && cols >= 1 && box_rows >= 1 && box_rows <= 256 && cols <= ld, ST_INTERNAL,
+                 "bad tensor map extents");
+  c.check_bytes(base, ((rows - 1) * ld + cols) * es, "tensor map extent");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(map, prec == MPSLCC_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  MPSLCC_REQUIRE(r == CUDA_SUCCESS, ST_CUDA, "cuTensorMapEncodeTiled failed");
+}
+
+int sm_count(Ctx& c) {
+  static int n = 0;
+  if (!n) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c.device);
+  return n > 0 ? n : 148;
+}
+
+// C (m x n, remapped rows) op= A (m x K) B (n x K)^T
+TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long ldb, int m, int n, int k, void* C,
+                 int ldc, int rpb, long long bstride, int mode, int ksplit_hint, long long soff = 0) {
+  TcTask t;
+  std::memset(&t, 0, sizeof(t));
+  const int KT = prec == MPSLCC_TF32 ? 32 : 64;
+  t.ntile = (int)std::min<long>(256, (n + 15) / 16 * 16);
+  encode_map(c, &t.ma, prec, A, m, k, lda, 128);
+  encode_map(c, &t.mb, prec, B, n, k, ldb, t.ntile);
+  t.C = C;
+  t.ldc = ldc;
+  t.rpb = rpb;
+  t.bstride = bstride;
+  t.m = m;
+  t.n = n;
+  t.k = k;
+  t.mode = mode;
+  t.ksteps = (k + KT - 1) / KT;
+  t.ksplit = std::max(1, std::min(ksplit_hint, t.ksteps));
+  t.kchunk = (t.ksteps + t.ksplit - 1) / t.ksplit;
+  t.ksplit = (t.ksteps + t.kchunk - 1) / t.kchunk;  // every split non-empty
+  t.tm = (m + 127) / 128;
+  t.tn = (n + t.ntile - 1) / t.ntile;
+  // output range check
+  const int es = (mode == 1 || mode == 3) ? 2 : 4;
+  long long last = (long long)((m - 1) / rpb) * bstride + (long long)((m - 1) % rpb) * ldc + (n - 1);
+  for (int r = 0; r < std::min(m, rpb); ++r) {
+    long long l2 = (long long)((m - 1 - r) / rpb) * bstride + (long long)((m - 1 - r) % rpb) * ldc + (n - 1);
+    last = std::max(last, l2);
+  }
+  if (mode == 3) last += 2 * soff;
+  t.soff = soff;
+  c.check_bytes(C, (last + 1) * es, "tc output");
+  return t;
+}
+
+long long plan_tc(std::vector<TcTask>& t) {
+  long long tot = 0;
+  for (auto& x : t) {
+    x.tile0 = tot;
+    tot += (long long)x.ksplit * x.tm * x.tn;
+  }
+  return tot;
+}
+
+void launch_tc(Ctx& c, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err) {
+  if (total <= 0 || ntasks <= 0) return;
+  int grid = (int)std::min<long long>(total, (long long)sm_count(c));
+  if (kprec(prec) == MPSLCC_BF16) {
+    static bool attr = false;
+    if (!attr) {
+      cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<MPSLCC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES),
+                 "smem attr");
+      attr = true;
+    }
+    tc_gemm_kernel<MPSLCC_BF16><<<grid, 128, SMEM_BYTES, c.s()>>>(d_tasks, ntasks, total, err);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<MPSLCC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      SMEM_BYTES),
+                 "smem attr");
+      attr = true;
+    }
+    tc_gemm_kernel<MPSLCC_TF32><<<grid, 128, SMEM_BYTES, c.s()>>>(d_tasks, ntasks, total, err);
+  }
+  cuda_check(cudaGetLastError(), "tc_gemm launch");
+  c.st.kernel_launches++;
+  c.st.gemm_launches++;
+}
+
+void run_conv(Ctx& c, int prec, std::vector<ConvTask>& t, DBuf& dtasks) {
+  if (t.empty()) return;
+  long long tot = 0;
+  const int es = esize(prec);
+  for (auto& x : t) {
+    c.check_range(x.src, 0, (long long)(x.batch - 1) * x.s_src + (long long)(x.rows - 1) * x.src_ld + x.cols - 1,
+                  "conv src");
+    c.check_bytes(x.dst, ((long long)(x.batch - 1) * x.s_dst + (long long)(x.rows - 1) * x.dst_ld + x.cols) * es,
+                  "conv dst");
+    x.tile0 = tot;
+    long long nel = (long long)x.rows * x.cols;
+    tot += (long long)x.batch * ((nel + CONV_CHUNK - 1) / CONV_CHUNK);
+  }
+  dtasks.ensure(&c, t.size() * sizeof(ConvTask));
+  cuda_check(cudaMemcpyAsync(dtasks.p, t.data(), t.size() * sizeof(ConvTask), cudaMemcpyHostToDevice, c.s()),
+             "conv tasks");
+  int grid = (int)std::min<long long>(tot, 152LL * 16);
+  if (kprec(prec) == MPSLCC_BF16) conv_kernel<MPSLCC_BF16><<<grid, 256, 0, c.s()>>>((const ConvTask*)dtasks.p, (int)t.size(), tot);
+  else conv_kernel<MPSLCC_TF32><<<grid, 256, 0, c.s()>>>((const ConvTask*)dtasks.p, (int)t.size(), tot);
+  cuda_check(cudaGetLastError(), "conv launch");
+  c.st.kernel_launches++;
+}
+
+void check_err(Ctx& c, DBuf& err) {
+  int h = 0;
+  cuda_check(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, c.s()), "tc err d2h");
+  cuda_check(cudaStreamSynchronize(c.s()), "tc sync");
+  if (h) {
+    cudaMemsetAsync(err.p, 0, sizeof(int), c.s());
+    throw Error(ST_TIMEOUT, "tensor-core kernel gave up waiting on an mbarrier (code " + std::to_string(h) + ")");
+  }
+}
+
+}  // namespace
+
+// Low-precision state of one sigma plan.
+struct TcState {
+  int prec = -1;
+  DBuf lcat, rstk, tt, x, y, t1, t2, conv, convx, err;
+  std::vector<long> lcat_off, K8, tt_off, x_off;
+  std::vector<long> stk_off;
+  std::vector<ConvTask> xconv;
+  int n1 = 0, n2 = 0;
+  long long tiles1 = 0, tiles2 = 0;
+  double bytes1 = 0, bytes2 = 0;
+};
+
+void tc_release(SigmaPlan& P) {
+  if (P.tc) {
+    delete P.tc;
+    P.tc = nullptr;
+  }
+}
+
+SigmaPlan::~SigmaPlan() { tc_release(*this); }
+
+void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
+  if (P.tc && P.tc->prec == prec) return;
+  tc_release(P);
+  TcState* S = new TcState();
+  P.tc = S;
+  S->prec = prec;
+  const int es = esize(prec);
+  // split mode: operands stored as three K blocks so that one product over
+  // 3K accumulates hi*hi + hi*lo + lo*hi (A blocks [hi|hi|lo], B [hi|lo|hi])
+  const int sp = prec == MPSLCC_BF16X3 ? 3 : 1;
+  const LeftFused& lf = P.lf;
+  const RightFused& rf = P.rf;
+  const size_t nbk = P.mid_b.size(), nkk = P.mid_k.size();
+  // padded K layout per bra key: each channel block width rounded up to 8
+  S->K8.assign(nbk, 0);
+  S->lcat_off.assign(nbk, 0);
+  S->tt_off.assign(nbk, 0);
+  std::vector<std::vector<long>> koff8(nbk);
+  long lsz = 0, tsz = 0;
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    long K8 = 0;
+    for (const auto& sg : lf.seg[bi]) {
+      koff8[bi].push_back(K8);
+      K8 += (long)sg.nw * pad8(sg.width);
+    }
+    S->K8[bi] = K8;
+    S->lcat_off[bi] = lsz;
+    S->tt_off[bi] = tsz;
+    lsz += pad8((long)lf.FLb.d[lf.kb[bi]] * sp * K8);
+    tsz += pad8((long)rf.FRb.d[rf.kb[bi]] * sp * K8);
+  }
+  S->stk_off.assign(rf.stk.size(), 0);
+  long ssz = 0;
+  for (size_t si = 0; si < rf.stk.size(); ++si) {
+    const auto& st = rf.stk[si];
+    S->stk_off[si] = ssz;
+    ssz += pad8((long)st.nw * rf.FRb.d[rf.kb[st.bidx]] * sp * pad8(rf.FRk.d[rf.kk[st.kidx]]));
+  }
+  S->x_off.assign(nkk, 0);
+  long xsz = 0;
+  for (size_t ki = 0; ki < nkk; ++ki) {
+    S->x_off[ki] = xsz;
+    xsz += pad8((long)lf.FLk.d[lf.kk[ki]] * sp * pad8(rf.FRk.d[rf.kk[ki]]));
+  }
+  auto zalloc = [&](DBuf& b, long elems, int e) {
+    b.alloc(&c, std::max<long>(elems * e, 16));
+    cuda_check(cudaMemsetAsync(b.p, 0, std::max<long>(elems * e, 16), c.s()), "tc memset");
+  };
+  zalloc(S->lcat, lsz, es);
+  zalloc(S->rstk, ssz, es);
+  zalloc(S->tt, tsz, es);
+  zalloc(S->x, xsz, es);
+  zalloc(S->y, std::max(P.nb, 1L), 4);
+  zalloc(S->err, 4, 1);
+  // FP64 -> low precision copies of L' and R'
+  std::vector<ConvTask> cv;
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    int rows = lf.FLb.d[lf.kb[bi]];
+    for (size_t g = 0; g < lf.seg[bi].size(); ++g) {
+      const auto& sg = lf.seg[bi][g];
+      ConvTask t;
+      std::memset(&t, 0, sizeof(t));
+      t.src = lf.data.d() + lf.off[bi] + sg.koff;
+      t.dst = (char*)S->lcat.p + (size_t)(S->lcat_off[bi] + koff8[bi][g]) * es;
+      t.rows = rows;
+      t.cols = sg.width;
+      t.src_ld = (int)lf.K[bi];
+      t.dst_ld = (int)(sp * S->K8[bi]);
+      t.batch = sg.nw;
+      t.s_src = sg.width;
+      t.s_dst = pad8(sg.width);
+      t.pattern = sp == 3 ? 1 : 0;
+      t.soff = S->K8[bi];
+      cv.push_back(t);
+    }
+  }
+  for (size_t si = 0; si < rf.stk.size(); ++si) {
+    const auto& st = rf.stk[si];
+    int rb = rf.FRb.d[rf.kb[st.bidx]], rk = rf.FRk.d[rf.kk[st.kidx]];
+    ConvTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.src = rf.data.d() + st.off;
+    t.dst = (char*)S->rstk.p + (size_t)S->stk_off[si] * es;
+    t.rows = st.nw * rb;
+    t.cols = rk;
+    t.src_ld = rk;
+    t.dst_ld = (int)(sp * pad8(rk));
+    t.batch = 1;
+    t.pattern = sp == 3 ? 1 : 0;
+    t.soff = pad8(rk);
+    cv.push_back(t);
+  }
+  run_conv(c, prec, cv, S->conv);
+  // per-call conversion of the input vector
+  S->xconv.clear();
+  for (size_t ki = 0; ki < nkk; ++ki) {
+    ConvTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.src = P.xin.d() + P.off_k[ki];
+    t.dst = (char*)S->x.p + (size_t)S->x_off[ki] * es;
+    t.rows = lf.FLk.d[lf.kk[ki]];
+    t.cols = rf.FRk.d[rf.kk[ki]];
+    t.src_ld = t.cols;
+    t.dst_ld = (int)(sp * pad8(t.cols));
+    t.batch = 1;
+    t.pattern = sp == 3 ? 2 : 0;
+    t.soff = pad8(t.cols);
+    S->xconv.push_back(t);
+  }
+  // phase 1: T_w^T = R'_w psi^T for all channels of a class in one tall GEMM
+  const int mode1 = sp == 3 ? 3 : (prec == MPSLCC_TF32 ? 2 : 1);
+  std::vector<TcTask> t1, t2;
+  for (size_t si = 0; si < rf.stk.size(); ++si) {
+    const auto& st = rf.stk[si];
+    int bi = st.bidx, ki = st.kidx;
+    const LeftFused::Seg* sg = lf.find_seg(bi, st.cls);
+    size_t g = sg - lf.seg[bi].data();
+    int rb = rf.FRb.d[rf.kb[bi]], rk = rf.FRk.d[rf.kk[ki]], lk = lf.FLk.d[lf.kk[ki]];
+    long kk = sp * pad8(rk);
+    void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + koff8[bi][g]) * es;
+    t1.push_back(make_task(c, prec, (char*)S->rstk.p + (size_t)S->stk_off[si] * es, kk,
+                           (char*)S->x.p + (size_t)S->x_off[ki] * es, kk, st.nw * rb, lk, (int)kk, C,
+                           (int)(sp * S->K8[bi]), rb, pad8(lk), mode1, 1, S->K8[bi]));
+    S->bytes1 += (double)es * sp * ((double)st.nw * rb * rk + (double)lk * rk + (double)st.nw * rb * lk);
+  }
+  // phase 2: sigma = Lcat Tt^T, split over K
+  long long base = 0;
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+    base += (long long)((lb + 127) / 128) * ((rb + 255) / 256);
+  }
+  const long long target = 2LL * sm_count(c);
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    if (S->K8[bi] == 0) continue;
+    int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+    long KK = sp * S->K8[bi];
+    int ks = (int)std::max(1LL, (target + base - 1) / std::max(1LL, base));
+    t2.push_back(make_task(c, prec, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, KK,
+                           (char*)S->tt.p + (size_t)S->tt_off[bi] * es, KK, lb, rb, (int)KK,
+                           (float*)S->y.p + P.off_b[bi], rb, 1 << 30, 0, 0, ks));
+    S->bytes2 += (double)es * ((double)lb * KK + (double)rb * KK) + 4.0 * lb * rb;
+  }
+  S->n1 = (int)t1.size();
+  S->n2 = (int)t2.size();
+  S->tiles1 = plan_tc(t1);
+  S->tiles2 = plan_tc(t2);
+  S->t1.alloc(&c, std::max<size_t>(t1.size(), 1) * sizeof(TcTask));
+  S->t2.alloc(&c, std::max<size_t>(t2.size(), 1) * sizeof(TcTask));
+  if (!t1.empty())
+    cuda_check(cudaMemcpyAsync(S->t1.p, t1.data(), t1.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
+               "tc tasks");
+  if (!t2.empty())
+    cuda_check(cudaMemcpyAsync(S->t2.p, t2.data(), t2.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
+               "tc tasks");
+  cuda_check(cudaStreamSynchronize(c.s()), "tc prepare sync");
+}
+
+void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
+  tc_prepare(c, P, prec);
+  TcState* S = P.tc;
+  if (P.nk > 0)
+    cuda_check(cudaMemcpyAsync(P.xin.p, x, P.nk * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma in");
+  std::vector<ConvTask> xc = S->xconv;
+  run_conv(c, S->prec, xc, S->convx);
+  cuda_check(cudaMemsetAsync(S->y.p, 0, std::max(P.nb, 1L) * 4, c.s()), "sigma zero");
+  cudaEventRecord(c.ev_p0, c.s());
+  launch_tc(c, S->prec, (const TcTask*)S->t1.p, S->n1, S->tiles1, (int*)S->err.p);
+  cudaEventRecord(c.ev_p1, c.s());
+  launch_tc(c, S->prec, (const TcTask*)S->t2.p, S->n2, S->tiles2, (int*)S->err.p);
+  cudaEventRecord(c.ev_p2, c.s());
+  launch_f32_to_f64(P.nb, (const float*)S->y.p, y, c.s());
+  c.st.kernel_launches++;
+  check_err(c, S->err);
+  float m1 = 0, m2 = 0;
+  cudaEventElapsedTime(&m1, c.ev_p0, c.ev_p1);
+  cudaEventElapsedTime(&m2, c.ev_p1, c.ev_p2);
+  c.st.tc_phase1_s += m1 * 1e-3;
+  c.st.tc_phase2_s += m2 * 1e-3;
+  c.st.tc_phase1_bytes += S->bytes1;
+  c.st.tc_phase2_bytes += S->bytes2;
+  c.st.tc_launches += 2;
+  c.st.sigma_calls++;
+  c.st.sigma_flops += P.flops;
+}
+
+// Stand-alone check of the tensor-core GEMM: C = A B^T (A m x k, B n x k,
+// FP64 host arrays) through one task of each output mode.
+void tc_selftest(Ctx& c, int prec, int m, int n, int k, const double* A, const double* B, double* C, int mode,
+                 int ksplit) {
+  const int es = esize(prec);
+  const int sp = prec == MPSLCC_BF16X3 ? 3 : 1;
+  long k8 = pad8(k), kk = sp * k8;
+  DBuf dA, dB, lA, lB, out, err, conv;
+  dA.alloc(&c, std::max<long>((long)m * k, 1) * 8);
+  dB.alloc(&c, std::max<long>((long)n * k, 1) * 8);
+  cuda_check(cudaMemcpyAsync(dA.p, A, (size_t)m * k * 8, cudaMemcpyHostToDevice, c.s()), "A");
+  cuda_check(cudaMemcpyAsync(dB.p, B, (size_t)n * k * 8, cudaMemcpyHostToDevice, c.s()), "B");
+  lA.alloc(&c, (size_t)m * kk * es);
+  lB.alloc(&c, (size_t)n * kk * es);
+  cuda_check(cudaMemsetAsync(lA.p, 0, (size_t)m * kk * es, c.s()), "z");
+  cuda_check(cudaMemsetAsync(lB.p, 0, (size_t)n * kk * es, c.s()), "z");
+  std::vector<ConvTask> cv(2);
+  std::memset(cv.data(), 0, sizeof(ConvTask) * 2);
+  cv[0].src = dA.d(); cv[0].dst = lA.p; cv[0].rows = m; cv[0].cols = k; cv[0].src_ld = k; cv[0].dst_ld = (int)kk;
+  cv[0].batch = 1; cv[0].pattern = sp == 3 ? 1 : 0; cv[0].soff = k8;
+  cv[1].src = dB.d(); cv[1].dst = lB.p; cv[1].rows = n; cv[1].cols = k; cv[1].src_ld = k; cv[1].dst_ld = (int)kk;
+  cv[1].batch = 1; cv[1].pattern = sp == 3 ? 2 : 0; cv[1].soff = k8;
+  run_conv(c, prec, cv, conv);
+  const int oes = mode == 1 ? 2 : 4;
+  out.alloc(&c, (size_t)m * n * oes);
+  cuda_check(cudaMemsetAsync(out.p, 0, (size_t)m * n * oes, c.s()), "z");
+  err.alloc(&c, 16);
+  cuda_check(cudaMemsetAsync(err.p, 0, 16, c.s()), "z");
+  std::vector<TcTask> t{make_task(c, prec, lA.p, kk, lB.p, kk, m, n, (int)kk, out.p, n, 1 << 30, 0, mode, ksplit)};
+  long long tiles = plan_tc(t);
+  DBuf dt;
+  dt.alloc(&c, sizeof(TcTask));
+  cuda_check(cudaMemcpyAsync(dt.p, t.data(), sizeof(TcTask), cudaMemcpyHostToDevice, c.s()), "task");
+  launch_tc(c, prec, (const TcTask*)dt.p, 1, tiles, (int*)err.p);
+  check_err(c, err);
+  if (mode == 1) {
+    std::vector<uint16_t> hb((size_t)m * n);
+    cuda_check(cudaMemcpy(hb.data(), out.p, hb.size() * 2, cudaMemcpyDeviceToHost), "d2h");
+    for (size_t i = 0; i < hb.size(); ++i) {
+      uint32_t u = (uint32_t)hb[i] << 16;
+      float f;
+      std::memcpy(&f, &u, 4);
+      C[i] = f;
+    }
+  } else {
+    std::vector<float> hf((size_t)m * n);
+    cuda_check(cudaMemcpy(hf.data(), out.p, hf.size() * 4, cudaMemcpyDeviceToHost), "d2h");
+    for (size_t i = 0; i < hf.size(); ++i) C[i] = hf[i];
+  }
 }
 
 }  // namespace mpslcc
