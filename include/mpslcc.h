@@ -124,6 +124,11 @@ typedef struct {
   double f64_phase1_seconds;/* device time of the FP64 sigma phases          */
   double f64_phase2_seconds;
   long long tc_launches;
+  double t_plan;            /* LCC sweep wall seconds: fused operators      */
+  double t_trunc;           /*   truncation (density matrix, FP64 eigh)      */
+  double t_env;             /*   environment renormalisation                 */
+  double t_solve;           /*   local linear solves                         */
+  double t_rhs;             /*   right-hand side, projector, diagonal        */
 } mpslcc_stats;
 
 /* Fill *opts with defaults (device 0, FP64, tol 1e-10, max_iter 200, auto

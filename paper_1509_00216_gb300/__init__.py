@@ -57,7 +57,8 @@ class Stats(C.Structure):
                 ("mpo_max_bond", C.c_int), ("tc_phase1_seconds", C.c_double), ("tc_phase2_seconds", C.c_double),
                 ("tc_phase1_bytes", C.c_double), ("tc_phase2_bytes", C.c_double),
                 ("f64_phase1_seconds", C.c_double), ("f64_phase2_seconds", C.c_double),
-                ("tc_launches", C.c_longlong)]
+                ("tc_launches", C.c_longlong), ("t_plan", C.c_double), ("t_trunc", C.c_double),
+                ("t_env", C.c_double), ("t_solve", C.c_double), ("t_rhs", C.c_double)]
 
 
 def _load():

@@ -140,7 +140,17 @@ mpslcc_status mpslcc_destroy(mpslcc_ctx* ctx) {
     for (DBuf* b : {&c.red, &c.red_out, &c.gtask, &c.ctask, &c.eig_work, &c.eig_w, &c.eig_info, &c.scratch_a,
                     &c.scratch_b})
       b->release();
+    for (int s = 0; s < Ctx::NEIG; ++s) {
+      c.eig_ws[s].release();
+      c.eig_inf[s].release();
+    }
     cudaStreamSynchronize(c.stream);
+    for (int s = 0; s < Ctx::NEIG; ++s) {
+      if (c.eig_solver[s]) cusolverDnDestroy(c.eig_solver[s]);
+      if (c.eig_stream[s]) cudaStreamDestroy(c.eig_stream[s]);
+      if (c.eig_ev[s]) cudaEventDestroy(c.eig_ev[s]);
+    }
+    if (c.eig_fork) cudaEventDestroy(c.eig_fork);
     if (c.solver) cusolverDnDestroy(c.solver);
     for (cudaEvent_t e : {c.ev0, c.ev1, c.ev_p0, c.ev_p1, c.ev_p2})
       if (e) cudaEventDestroy(e);
@@ -515,6 +525,11 @@ mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out) {
     out->f64_phase1_seconds = c.st.f64_phase1_s;
     out->f64_phase2_seconds = c.st.f64_phase2_s;
     out->tc_launches = c.st.tc_launches;
+    out->t_plan = c.st.t_plan;
+    out->t_trunc = c.st.t_trunc;
+    out->t_env = c.st.t_env;
+    out->t_solve = c.st.t_solve;
+    out->t_rhs = c.st.t_rhs;
   });
 }
 

@@ -14,8 +14,23 @@
 
 #include <cmath>
 #include <cstring>
+#include <ctime>
 
 namespace mpslcc {
+
+static double now_s() {
+  timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return ts.tv_sec + 1e-9 * ts.tv_nsec;
+}
+StageTimer::StageTimer(Ctx& c_, double* a) : c(c_), acc(a) {
+  cudaStreamSynchronize(c.s());
+  t0 = now_s();
+}
+StageTimer::~StageTimer() {
+  cudaStreamSynchronize(c.s());
+  *acc += now_s() - t0;
+}
 
 void cuda_check(cudaError_t e, const char* what) {
   if (e != cudaSuccess)

@@ -176,6 +176,17 @@ struct Stats {
   double tc_phase1_s = 0, tc_phase2_s = 0, tc_phase1_bytes = 0, tc_phase2_bytes = 0;
   double f64_phase1_s = 0, f64_phase2_s = 0;
   long long tc_launches = 0;
+  // host wall time per sweep stage (stream-synchronised)
+  double t_plan = 0, t_trunc = 0, t_env = 0, t_solve = 0, t_rhs = 0;
+};
+
+// Adds the wall time of a scope (after synchronising the stream) to *acc.
+struct StageTimer {
+  Ctx& c;
+  double* acc;
+  double t0;
+  StageTimer(Ctx& c_, double* a);
+  ~StageTimer();
 };
 
 struct Ctx {
@@ -218,6 +229,11 @@ struct Ctx {
   // scratch
   DBuf red, red_out, gtask, ctask;
   DBuf eig_work, eig_w, eig_info;
+  static constexpr int NEIG = 8;   // concurrent eigensolver streams
+  cudaStream_t eig_stream[NEIG] = {};
+  cusolverDnHandle_t eig_solver[NEIG] = {};
+  cudaEvent_t eig_ev[NEIG] = {}, eig_fork = nullptr;
+  DBuf eig_ws[NEIG], eig_inf[NEIG];
   DBuf scratch_a, scratch_b;
 
   cudaStream_t s() const { return stream; }

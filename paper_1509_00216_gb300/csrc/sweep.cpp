@@ -103,7 +103,7 @@ void sigma_timed(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
 
 // Davidson for the lowest eigenpair of the local H_eff (reference, Eq. EH).
 double davidson(Ctx& c, SigmaPlan& P, double* x, long n, const double* diag, double tol, int maxit, int maxsub,
-                bool* converged) {
+                bool* converged, int prec) {
   maxsub = std::max(4, std::min(maxsub, (int)std::max(1L, n)));
   DBuf Vb, AVb;
   Vb.alloc(&c, (size_t)maxsub * n * sizeof(double));
@@ -121,7 +121,7 @@ double davidson(Ctx& c, SigmaPlan& P, double* x, long n, const double* diag, dou
   }
   copyv(c, V, x, n);
   launch_scale(n, 1.0 / nx, V, c.s());
-  sigma_timed(c, P, V, AV, MPSLCC_FP64);
+  sigma_timed(c, P, V, AV, prec);
   int m = 1;
   std::vector<double> Hs(1, dev_dot(c, V, AV, n));
   double theta = Hs[0];
@@ -171,7 +171,7 @@ double davidson(Ctx& c, SigmaPlan& P, double* x, long n, const double* diag, dou
       launch_scale(n, 1.0 / tn2, t.d(), c.s());
     }
     copyv(c, V + (long)m * n, t.d(), n);
-    sigma_timed(c, P, V + (long)m * n, AV + (long)m * n, MPSLCC_FP64);
+    sigma_timed(c, P, V + (long)m * n, AV + (long)m * n, prec);
     std::vector<double> col = multidot(c, V, n, m + 1, AV + (long)m * n, n);
     std::vector<double> H2((size_t)(m + 1) * (m + 1));
     for (int i = 0; i < m; ++i)
@@ -362,24 +362,47 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     gt.push_back(t);
   }
   run_gemms(c, gt);
-  // FP64 eigendecompositions (cuSOLVER), eigenvalues ascending
-  int lwork = 0;
-  for (int i = 0; i < ns; ++i) {
-    int lw = 0;
-    cusolverDnDsyevd_bufferSize(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i], rho.d() + roff[i],
-                                nd[i], w.d() + woff[i], &lw);
-    lwork = std::max(lwork, lw);
+  // FP64 eigendecompositions (cuSOLVER), eigenvalues ascending.  The
+  // sectors are independent: they run concurrently on NEIG side streams,
+  // largest first, each stream with its own handle and workspace.
+  if (!c.eig_solver[0]) {
+    for (int s = 0; s < Ctx::NEIG; ++s) {
+      cuda_check(cudaStreamCreateWithFlags(&c.eig_stream[s], cudaStreamNonBlocking), "eig stream");
+      MPSLCC_REQUIRE(cusolverDnCreate(&c.eig_solver[s]) == CUSOLVER_STATUS_SUCCESS, ST_CUDA, "cusolverDnCreate");
+      cusolverDnSetStream(c.eig_solver[s], c.eig_stream[s]);
+      cuda_check(cudaEventCreateWithFlags(&c.eig_ev[s], cudaEventDisableTiming), "eig event");
+    }
+    cuda_check(cudaEventCreateWithFlags(&c.eig_fork, cudaEventDisableTiming), "eig event");
   }
-  c.eig_work.ensure(&c, (size_t)std::max(lwork, 1) * sizeof(double));
-  c.eig_info.ensure(&c, sizeof(int) * 4);
-  for (int i = 0; i < ns; ++i) {
+  std::vector<int> order(ns);
+  for (int i = 0; i < ns; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nd[a] > nd[b]; });
+  int lwork[Ctx::NEIG] = {0};
+  for (int t = 0; t < ns; ++t) {
+    int i = order[t], sidx = t % Ctx::NEIG, lw = 0;
+    cusolverDnDsyevd_bufferSize(c.eig_solver[sidx], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i],
+                                rho.d() + roff[i], nd[i], w.d() + woff[i], &lw);
+    lwork[sidx] = std::max(lwork[sidx], lw);
+  }
+  for (int sidx = 0; sidx < Ctx::NEIG; ++sidx) {
+    c.eig_ws[sidx].ensure(&c, (size_t)std::max(lwork[sidx], 1) * sizeof(double));
+    c.eig_inf[sidx].ensure(&c, sizeof(int) * 4);
+  }
+  cuda_check(cudaEventRecord(c.eig_fork, c.s()), "eig fork");
+  for (int sidx = 0; sidx < Ctx::NEIG; ++sidx) cudaStreamWaitEvent(c.eig_stream[sidx], c.eig_fork, 0);
+  for (int t = 0; t < ns; ++t) {
+    int i = order[t], sidx = t % Ctx::NEIG;
     c.check_range(rho.d() + roff[i], 0, (long long)nd[i] * nd[i] - 1, "eigh matrix");
     c.check_range(w.d() + woff[i], 0, nd[i] - 1, "eigh values");
-    cusolverStatus_t st = cusolverDnDsyevd(c.solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i],
-                                           rho.d() + roff[i], nd[i], w.d() + woff[i], c.eig_work.d(), lwork,
-                                           (int*)c.eig_info.p);
+    cusolverStatus_t st = cusolverDnDsyevd(c.eig_solver[sidx], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                           nd[i], rho.d() + roff[i], nd[i], w.d() + woff[i], c.eig_ws[sidx].d(),
+                                           lwork[sidx], (int*)c.eig_inf[sidx].p);
     MPSLCC_REQUIRE(st == CUSOLVER_STATUS_SUCCESS, ST_CUDA, "cusolverDnDsyevd failed");
     c.st.kernel_launches++;
+  }
+  for (int sidx = 0; sidx < Ctx::NEIG; ++sidx) {
+    cuda_check(cudaEventRecord(c.eig_ev[sidx], c.eig_stream[sidx]), "eig join");
+    cudaStreamWaitEvent(c.s(), c.eig_ev[sidx], 0);
   }
   std::vector<double> hw(std::max(wtot, 1L));
   cuda_check(cudaMemcpyAsync(hw.data(), w.p, wtot * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "eig d2h");
@@ -618,8 +641,16 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
         form_two_site(c, c.phi0, l, x.d());
         sigma_diag(c, P, dg.d());
         bool conv = false;
-        E = davidson(c, P, x.d(), n, dg.d(), std::max(c.opts.tol, 1e-13), c.opts.max_iter,
-                     c.opts.davidson_max_subspace, &conv);
+        // low-precision products (split BF16 in mixed mode) for the search;
+        // the reported energy is an FP64 Rayleigh quotient at the last position
+        const int dprec = c.opts.prec == MPSLCC_FP64 ? MPSLCC_FP64 : MPSLCC_BF16X3;
+        const bool last = sw == n_sweeps - 1 && !right && l == 0;
+        // split-BF16 products reach a residual of ~2^-16 |H_eff|: stop there
+        double dtol = dprec == MPSLCC_FP64 ? std::max(c.opts.tol, 1e-13) : std::max(c.opts.tol, 1e-4);
+        E = davidson(c, P, x.d(), n, dg.d(), dtol, c.opts.max_iter, c.opts.davidson_max_subspace, &conv, dprec);
+        if (dprec != MPSLCC_FP64 && last)  // FP64 polish of the reported eigenpair
+          E = davidson(c, P, x.d(), n, dg.d(), std::max(c.opts.tol, 1e-13), c.opts.max_iter,
+                       c.opts.davidson_max_subspace, &conv, MPSLCC_FP64);
         all_conv &= conv;
         double disc = truncate(c, c.phi0, l, x.d(), M0, right);
         c.max_disc = std::max(c.max_disc, disc);
@@ -664,9 +695,14 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
       for (int step = 0; step <= k - 2; ++step) {
         int l = right ? step : k - 2 - step;
         SigmaPlan P11, P10, PS;
-        make_sigma_plan(c, c.f11, l, P11);
-        make_sigma_plan(c, c.f10, l, P10);
-        make_sigma_plan(c, c.s10, l, PS);
+        {
+          StageTimer tm(c, &c.st.t_plan);
+          make_sigma_plan(c, c.f11, l, P11);
+          make_sigma_plan(c, c.f10, l, P10);
+          make_sigma_plan(c, c.s10, l, PS);
+          if (prec != MPSLCC_FP64) tc_prepare(c, P11, MPSLCC_BF16X3);
+        }
+        StageTimer* trhs = new StageTimer(c, &c.st.t_rhs);
         long n = P11.nk, n0 = P10.nk;
         DBuf xb, bb, ub, vb, sb, dg, p0;
         xb.alloc(&c, std::max(n, 1L) * sizeof(double));
@@ -690,6 +726,8 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
         project(c, u, bb.d(), n);
         form_two_site(c, c.phi1, l, xb.d());
         sigma_diag(c, P11, dg.d());
+        delete trhs;
+        StageTimer* tsol = new StageTimer(c, &c.st.t_solve);
         LinOp A{&P11, c.E0, u, Vec()};
         int its = 0;
         bool indef = false;
@@ -729,12 +767,18 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
         A.apply(c, xb.d(), ax.d(), jprec);
         J = dev_dot(c, xb.d(), ax.d(), n) - 2.0 * dev_dot(c, xb.d(), bb.d(), n);
         E2 = J;
-        double disc = truncate(c, c.phi1, l, xb.d(), M1, right);
+        delete tsol;
+        double disc;
+        {
+          StageTimer tm(c, &c.st.t_trunc);
+          disc = truncate(c, c.phi1, l, xb.d(), M1, right);
+        }
         c.max_disc = std::max(c.max_disc, disc);
         for (Family* F : {&c.f11, &c.f10, &c.s10}) {
           invalidate_site(*F, l);
           invalidate_site(*F, l + 1);
         }
+        StageTimer tenv(c, &c.st.t_env);
         if (right) {
           env_update_left(c, c.f11, l, P11.lf);
           env_update_left(c, c.f10, l, P10.lf);

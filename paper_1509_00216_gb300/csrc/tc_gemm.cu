@@ -257,6 +257,44 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restric
         const int c0 = col0 + cb;
         const int nv = min(32, T->n - c0);
         if (nv <= 0) continue;
+        if (T->mode == 1 || T->mode == 3) {
+          // BF16 rows: a thread owns 32 contiguous outputs = 64 bytes; store
+          // them as four 16-byte vectors when aligned
+          __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
+          if (nv == 32 && ((uintptr_t)C & 15) == 0 && (T->mode == 1 || (T->soff & 7) == 0)) {
+            uint32_t hi[16], lo[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
+              const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+              const float2 hf = __bfloat1622float2(h);
+              const __nv_bfloat162 l = __floats2bfloat162_rn(f0 - hf.x, f1 - hf.y);
+              hi[j] = *reinterpret_cast<const uint32_t*>(&h);
+              lo[j] = *reinterpret_cast<const uint32_t*>(&l);
+            }
+            uint4* d0 = reinterpret_cast<uint4*>(C);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) d0[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+            if (T->mode == 3) {
+              uint4* d1 = reinterpret_cast<uint4*>(C + T->soff);
+              uint4* d2 = reinterpret_cast<uint4*>(C + 2 * T->soff);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                d1[q] = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+                d2[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+              }
+            }
+            continue;
+          }
+        }
+        if (T->mode == 2 && nv == 32 && (((uintptr_t)((float*)T->C + roff + c0)) & 15) == 0) {
+          float4* d = reinterpret_cast<float4*>((float*)T->C + roff + c0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            d[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
+                               __uint_as_float(v[4 * q + 3]));
+          continue;
+        }
         if (T->mode == 0) {
           float* C = (float*)T->C + roff + c0;
           for (int j = 0; j < nv; ++j) atomicAdd(C + j, __uint_as_float(v[j]));
