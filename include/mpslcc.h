@@ -227,6 +227,29 @@ mpslcc_status mpslcc_export_mpo_site(mpslcc_ctx* ctx, int which, int site, int* 
 mpslcc_status mpslcc_debug_tc_gemm(mpslcc_ctx* ctx, int prec, int m, int n, int k, const double* A,
                                    const double* B, double* C, int mode, int ksplit);
 
+/* Allocation-free C = A B^T (the product of mpslcc_debug_tc_gemm with FP32
+   output) for callers that cannot allocate device memory when they need it:
+   code recorded under CUDA stream capture, or a host framework that owns every
+   device allocation and forbids new ones inside its step.  There is no
+   counterpart in the paper.
+   - d_A (m x k), d_B (n x k), d_C (m x n): row-major FP64 DEVICE arrays owned
+     by the caller; prec is TF32, BF16 or BF16X3; work runs on `stream` (NULL =
+     legacy default stream) of `device`, which must be the current device.
+   - The call allocates nothing and needs no context: its operand copies, FP32
+     result, task descriptors and error flag live in one file-scope device
+     array of mpslcc_tc_gemm_noalloc_scratch_bytes() bytes (64 MiB), reserved
+     on every GPU that loads the library until the process exits.  Problems
+     whose scratch would exceed it return MPSLCC_E_ARG.
+   - The first call on a device looks up the array's device address (set-up);
+     make that first call before any stream capture.
+   - Every call reuses the same array and overwrites what it needs (padding
+     is cleared each call); calls that overlap on the GPU, from any stream or
+     thread, race on it.  The call synchronises `stream` to read the kernel's
+     error flag.  Returns MPSLCC_E_TIMEOUT if the kernel gave up waiting. */
+mpslcc_status mpslcc_tc_gemm_noalloc(int device, void* stream, int prec, int m, int n, int k, const double* d_A,
+                                     const double* d_B, double* d_C);
+size_t mpslcc_tc_gemm_noalloc_scratch_bytes(void);
+
 mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out);
 mpslcc_status mpslcc_reset_stats(mpslcc_ctx* ctx);
 

@@ -28,7 +28,7 @@ EXPORTED = [
     "mpslcc_set_spaces", "mpslcc_dmrg_reference", "mpslcc_lcc_sweep", "mpslcc_energy", "mpslcc_local_dim",
     "mpslcc_apply_heff", "mpslcc_apply_heff_device", "mpslcc_load_mps", "mpslcc_export_mps",
     "mpslcc_mpo_bond_dims", "mpslcc_export_mpo_site", "mpslcc_get_stats", "mpslcc_reset_stats",
-    "mpslcc_debug_tc_gemm",
+    "mpslcc_debug_tc_gemm", "mpslcc_tc_gemm_noalloc", "mpslcc_tc_gemm_noalloc_scratch_bytes",
 ]
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -89,6 +89,8 @@ def _load():
         "mpslcc_get_stats": (C.c_int, [vp, C.POINTER(Stats)]),
         "mpslcc_reset_stats": (C.c_int, [vp]),
         "mpslcc_debug_tc_gemm": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, C.c_int]),
+        "mpslcc_tc_gemm_noalloc": (C.c_int, [C.c_int, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]),
+        "mpslcc_tc_gemm_noalloc_scratch_bytes": (C.c_size_t, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -119,6 +121,14 @@ def _dptr(a):
 
 def _iptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def tc_gemm_noalloc(device, stream, prec, m, n, k, d_A, d_B, d_C):
+    """C = A B^T with no device allocation (device pointers; see the header)."""
+    st = lib().mpslcc_tc_gemm_noalloc(device, C.c_void_p(stream), prec, m, n, k, C.c_void_p(d_A),
+                                      C.c_void_p(d_B), C.c_void_p(d_C))
+    if st != 0:
+        raise MpsLccError(st, "mpslcc_tc_gemm_noalloc failed")
 
 
 class Context:

@@ -545,6 +545,21 @@ mpslcc_status mpslcc_debug_tc_gemm(mpslcc_ctx* ctx, int prec, int m, int n, int 
   });
 }
 
+mpslcc_status mpslcc_tc_gemm_noalloc(int device, void* stream, int prec, int m, int n, int k, const double* d_A,
+                                     const double* d_B, double* d_C) {
+  try {
+    tc_gemm_noalloc(device, (cudaStream_t)stream, prec, m, n, k, d_A, d_B, d_C);
+    return MPSLCC_OK;
+  } catch (const Error& e) {
+    cudaGetLastError();
+    return (mpslcc_status)e.status;
+  } catch (...) {
+    return MPSLCC_E_INTERNAL;
+  }
+}
+
+size_t mpslcc_tc_gemm_noalloc_scratch_bytes(void) { return tc_gemm_noalloc_max_bytes(); }
+
 mpslcc_status mpslcc_reset_stats(mpslcc_ctx* ctx) {
   return guard(ctx, [&](Ctx& c) { c.st = Stats(); });
 }

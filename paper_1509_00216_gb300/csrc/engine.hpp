@@ -275,6 +275,9 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec);
 void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec);
 void tc_selftest(Ctx& c, int prec, int m, int n, int k, const double* A, const double* B, double* C, int mode,
                  int ksplit);
+size_t tc_gemm_noalloc_max_bytes();
+void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, int k, const double* dA,
+                     const double* dB, double* dC);
 
 // sweeps (sweep.cpp)
 void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed);

@@ -16,6 +16,8 @@
 #include <cuda_bf16.h>
 
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "engine.hpp"
 
@@ -788,6 +790,135 @@ void tc_selftest(Ctx& c, int prec, int m, int n, int k, const double* A, const d
     cuda_check(cudaMemcpy(hf.data(), out.p, hf.size() * 4, cudaMemcpyDeviceToHost), "d2h");
     for (size_t i = 0; i < hf.size(); ++i) C[i] = hf[i];
   }
+}
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the tensor-core GEMM.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// product: code recorded under CUDA stream capture, or a host framework that
+// owns every device allocation and forbids new ones inside its step.  For
+// them, C = A B^T (the self-test product above) is also offered with all of
+// its scratch -- the low-precision operand copies, the FP32 result, the task
+// descriptors and the error flag -- in one fixed file-scope device array.
+// ---------------------------------------------------------------------------
+constexpr size_t NOALLOC_SCRATCH_BYTES = 64ull << 20;  // 64 MiB held by every GPU that loads the library
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[128] = {};
+
+// Device address of the scratch array for the current device (host code sees
+// only a host-side stand-in for the symbol, so it must be looked up per device).
+void* noalloc_scratch(int device) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  MPSLCC_REQUIRE(device >= 0 && device < 128, ST_ARG, "device ordinal out of range");
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
+    g_noalloc_ptr[device] = p;
+  }
+  return g_noalloc_ptr[device];
+}
+
+inline size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+void noalloc_map(CUtensorMap* map, int prec, const void* base, long rows, long cols, long ld, int box_rows) {
+  const int es = esize(prec);
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(map, prec == MPSLCC_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  MPSLCC_REQUIRE(r == CUDA_SUCCESS, ST_CUDA, "cuTensorMapEncodeTiled failed");
+}
+}  // namespace
+
+size_t tc_gemm_noalloc_max_bytes() { return NOALLOC_SCRATCH_BYTES; }
+
+void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, int k, const double* dA,
+                     const double* dB, double* dC) {
+  MPSLCC_REQUIRE(prec >= MPSLCC_TF32 && prec <= MPSLCC_BF16X3, ST_ARG, "prec must be TF32, BF16 or BF16X3");
+  MPSLCC_REQUIRE(m >= 1 && n >= 1 && k >= 1 && dA && dB && dC, ST_ARG, "bad argument");
+  const int es = esize(prec);
+  const int sp = prec == MPSLCC_BF16X3 ? 3 : 1;
+  const long k8 = pad8(k), kk = sp * k8;
+  // scratch layout: [conv tasks | tc task | error flag | A copy | B copy | FP32 result]
+  const size_t o_conv = 0, o_task = up256(2 * sizeof(ConvTask)), o_err = o_task + up256(sizeof(TcTask));
+  const size_t o_a = o_err + 256, o_b = o_a + up256((size_t)m * kk * es), o_c = o_b + up256((size_t)n * kk * es);
+  const size_t need = o_c + up256((size_t)m * n * 4);
+  MPSLCC_REQUIRE(need <= NOALLOC_SCRATCH_BYTES, ST_ARG,
+                 "problem needs " + std::to_string(need) + " scratch bytes; the allocation-free GEMM holds " +
+                     std::to_string(NOALLOC_SCRATCH_BYTES));
+  int cur = -1;
+  cuda_check(cudaGetDevice(&cur), "cudaGetDevice");
+  MPSLCC_REQUIRE(cur == device, ST_ARG, "device must be the current device");
+  char* base = (char*)noalloc_scratch(device);
+  // operand copies: zero padding columns, then convert
+  cuda_check(cudaMemsetAsync(base + o_err, 0, 256, stream), "noalloc memset");
+  cuda_check(cudaMemsetAsync(base + o_a, 0, o_c - o_a, stream), "noalloc memset");
+  ConvTask cv[2];
+  std::memset(cv, 0, sizeof(cv));
+  cv[0].src = dA; cv[0].dst = base + o_a; cv[0].rows = m; cv[0].cols = k; cv[0].src_ld = k; cv[0].dst_ld = (int)kk;
+  cv[0].batch = 1; cv[0].pattern = sp == 3 ? 1 : 0; cv[0].soff = k8;
+  cv[1].src = dB; cv[1].dst = base + o_b; cv[1].rows = n; cv[1].cols = k; cv[1].src_ld = k; cv[1].dst_ld = (int)kk;
+  cv[1].batch = 1; cv[1].pattern = sp == 3 ? 2 : 0; cv[1].soff = k8;
+  long long tot = 0;
+  for (auto& x : cv) {
+    x.tile0 = tot;
+    tot += ((long long)x.rows * x.cols + CONV_CHUNK - 1) / CONV_CHUNK;
+  }
+  cuda_check(cudaMemcpyAsync(base + o_conv, cv, sizeof(cv), cudaMemcpyHostToDevice, stream), "noalloc tasks");
+  int cgrid = (int)std::min<long long>(tot, 152LL * 16);
+  if (kprec(prec) == MPSLCC_BF16) conv_kernel<MPSLCC_BF16><<<cgrid, 256, 0, stream>>>((const ConvTask*)(base + o_conv), 2, tot);
+  else conv_kernel<MPSLCC_TF32><<<cgrid, 256, 0, stream>>>((const ConvTask*)(base + o_conv), 2, tot);
+  cuda_check(cudaGetLastError(), "noalloc conv");
+  // one GEMM task writing FP32 rows of C
+  TcTask t;
+  std::memset(&t, 0, sizeof(t));
+  const int KT = prec == MPSLCC_TF32 ? 32 : 64;
+  t.ntile = (int)std::min<long>(256, (n + 15) / 16 * 16);
+  noalloc_map(&t.ma, prec, base + o_a, m, kk, kk, 128);
+  noalloc_map(&t.mb, prec, base + o_b, n, kk, kk, t.ntile);
+  t.C = base + o_c;
+  t.ldc = n;
+  t.rpb = 1 << 30;
+  t.m = m;
+  t.n = n;
+  t.k = (int)kk;
+  t.mode = 2;
+  t.ksteps = (int)((kk + KT - 1) / KT);
+  t.ksplit = 1;
+  t.kchunk = t.ksteps;
+  t.tm = (m + 127) / 128;
+  t.tn = (n + t.ntile - 1) / t.ntile;
+  t.tile0 = 0;
+  long long tiles = (long long)t.tm * t.tn;
+  cuda_check(cudaMemcpyAsync(base + o_task, &t, sizeof(t), cudaMemcpyHostToDevice, stream), "noalloc task");
+  int grid = (int)std::min<long long>(tiles, 148);
+  if (kprec(prec) == MPSLCC_BF16) {
+    cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<MPSLCC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES), "smem attr");
+    tc_gemm_kernel<MPSLCC_BF16><<<grid, 128, SMEM_BYTES, stream>>>((const TcTask*)(base + o_task), 1, tiles,
+                                                                    (int*)(base + o_err));
+  } else {
+    cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<MPSLCC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES), "smem attr");
+    tc_gemm_kernel<MPSLCC_TF32><<<grid, 128, SMEM_BYTES, stream>>>((const TcTask*)(base + o_task), 1, tiles,
+                                                                    (int*)(base + o_err));
+  }
+  cuda_check(cudaGetLastError(), "noalloc gemm");
+  launch_f32_to_f64((long)m * n, (const float*)(base + o_c), dC, stream);
+  cuda_check(cudaGetLastError(), "noalloc result");
+  int h = 0;
+  cuda_check(cudaMemcpyAsync(&h, base + o_err, sizeof(int), cudaMemcpyDeviceToHost, stream), "noalloc flag");
+  cuda_check(cudaStreamSynchronize(stream), "noalloc sync");
+  if (h) throw Error(ST_TIMEOUT, "tensor-core kernel gave up waiting on an mbarrier");
 }
 
 }  // namespace mpslcc
