@@ -138,7 +138,7 @@ mpslcc_status mpslcc_destroy(mpslcc_ctx* ctx) {
     c.phi1 = MPS();
     for (auto& b : c.boxes) b.release();
     for (DBuf* b : {&c.red, &c.red_out, &c.gtask, &c.ctask, &c.eig_work, &c.eig_w, &c.eig_info, &c.scratch_a,
-                    &c.scratch_b})
+                    &c.scratch_b, &c.scratch_tc, &c.tc_conv_tasks, &c.tc_gemm_tasks, &c.tc_err})
       b->release();
     for (int s = 0; s < Ctx::NEIG; ++s) {
       c.eig_ws[s].release();
@@ -254,10 +254,10 @@ mpslcc_status mpslcc_energy(mpslcc_ctx* ctx, mpslcc_energies* out) {
   return guard(ctx, [&](Ctx& c) {
     MPSLCC_REQUIRE(out, ST_ARG, "null output");
     MPSLCC_REQUIRE(c.have_E0, ST_STATE, "no reference energy yet");
-    if (c.have_E2 && !c.e3_valid) {
+    if (c.have_E2 && !c.e_valid) {  // FP64 evaluation of the current state
       need_device(c);
       cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
-      compute_e3(c);
+      compute_energies(c);
     }
     std::memset(out, 0, sizeof(*out));
     out->E0 = c.E0;

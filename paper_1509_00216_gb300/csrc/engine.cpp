@@ -165,6 +165,11 @@ void run_gemms(Ctx& c, std::vector<GemmTask>& t) {
   c.st.kernel_launches++;
 }
 
+void run_gemm_tasks(Ctx& c, std::vector<GemmTask>& t) {
+  if (c.gemm_prec == MPSLCC_FP64) run_gemms(c, t);
+  else run_gemms_tc(c, t);
+}
+
 void run_copies(Ctx& c, std::vector<CopyTask>& t) {
   if (t.empty()) return;
   for (const auto& x : t) validate_copy(c, x);
@@ -436,7 +441,7 @@ void make_left_fused(Ctx& c, Family& F, int p, const std::vector<QN>& kbq, const
     }
   }
   run_copies(c, ct);
-  run_gemms(c, gt);
+  run_gemm_tasks(c, gt);
 }
 
 void make_right_fused(Ctx& c, Family& F, int p, const std::vector<QN>& kbq, const std::vector<QN>& kkq,
@@ -502,7 +507,7 @@ void make_right_fused(Ctx& c, Family& F, int p, const std::vector<QN>& kbq, cons
     }
   }
   run_copies(c, ct);
-  run_gemms(c, gt);
+  run_gemm_tasks(c, gt);
 }
 
 void env_update_left(Ctx& c, Family& F, int p, const LeftFused& lf) {
@@ -551,8 +556,8 @@ void env_update_left(Ctx& c, Family& F, int p, const LeftFused& lf) {
                       (long long)rows * dk, (long long)db * dk));
     c.st.env_flops += 2.0 * j.sg->nw * ((double)rows * dk * j.sg->width + (double)db * dk * rows);
   }
-  run_gemms(c, tx);
-  run_gemms(c, ty);
+  run_gemm_tasks(c, tx);
+  run_gemm_tasks(c, ty);
   ne.valid = true;
   F.L[p + 1] = std::move(ne);
 }
@@ -603,8 +608,8 @@ void env_update_right(Ctx& c, Family& F, int p, const RightFused& rf) {
                       (long long)rb * dk, (long long)db * dk));
     c.st.env_flops += 2.0 * j.S->nw * ((double)rb * dk * rk + (double)db * dk * rb);
   }
-  run_gemms(c, ty);
-  run_gemms(c, tz);
+  run_gemm_tasks(c, ty);
+  run_gemm_tasks(c, tz);
   ne.valid = true;
   F.R[p] = std::move(ne);
 }
@@ -821,7 +826,7 @@ void sigma_diag(Ctx& c, SigmaPlan& P, double* diag) {
     cuda_check(cudaGetLastError(), "gather launch");
     cuda_check(cudaStreamSynchronize(c.s()), "gather sync");
   }
-  run_gemms(c, mt);
+  run_gemm_tasks(c, mt);
 }
 
 void form_two_site(Ctx& c, MPS& m, int l, double* psi) {
@@ -842,7 +847,7 @@ void form_two_site(Ctx& c, MPS& m, int l, double* psi) {
     t.push_back(gemm(m.site[l].lf.d() + m.site[l].lf_off[j], m.site[l + 1].rf.d() + m.site[l + 1].rf_off[j],
                      psi + off[i], dl, dr, dj, dj, dr, dr));
   }
-  run_gemms(c, t);
+  run_gemm_tasks(c, t);
 }
 
 }  // namespace mpslcc

@@ -176,6 +176,7 @@ struct Stats {
   double tc_phase1_s = 0, tc_phase2_s = 0, tc_phase1_bytes = 0, tc_phase2_bytes = 0;
   double f64_phase1_s = 0, f64_phase2_s = 0;
   long long tc_launches = 0;
+  double tc_gemm_flops = 0;
   // host wall time per sweep stage (stream-synchronised)
   double t_plan = 0, t_trunc = 0, t_env = 0, t_solve = 0, t_rhs = 0;
 };
@@ -214,7 +215,7 @@ struct Ctx {
   DBuf boxes[4];
   MPS phi0, phi1;
   double E0 = 0, E2 = 0, E3 = 0, J = 0, ovl01 = 0, norm1 = 0, max_disc = 0;
-  bool have_E0 = false, have_E2 = false, e3_valid = false;
+  bool have_E0 = false, have_E2 = false, e3_valid = false, e_valid = false;
   int sweeps_done = 0;
   Stats st;
 
@@ -235,6 +236,10 @@ struct Ctx {
   cudaEvent_t eig_ev[NEIG] = {}, eig_fork = nullptr;
   DBuf eig_ws[NEIG], eig_inf[NEIG];
   DBuf scratch_a, scratch_b;
+  DBuf scratch_tc, tc_conv_tasks, tc_gemm_tasks, tc_err;
+  // precision of the per-site FP64 GEMM tasks (fusion, renormalisation,
+  // truncation): MPSLCC_FP64, or MPSLCC_BF16X3 inside mixed-precision sweeps
+  int gemm_prec = MPSLCC_FP64;
 
   cudaStream_t s() const { return stream; }
 };
@@ -242,6 +247,9 @@ struct Ctx {
 // ---- engine entry points (engine.cpp / sweep.cpp) ----
 void upload_boxes(Ctx& c, int which);
 void run_gemms(Ctx& c, std::vector<GemmTask>& t);
+void run_gemms_tc(Ctx& c, std::vector<GemmTask>& t);
+// FP64 DFMA kernel or split-BF16 tensor cores, by c.gemm_prec
+void run_gemm_tasks(Ctx& c, std::vector<GemmTask>& t);
 void validate_gemm(const Ctx& c, const GemmTask& t);
 void validate_copy(const Ctx& c, const CopyTask& t);
 void run_copies(Ctx& c, std::vector<CopyTask>& t);
@@ -284,5 +292,6 @@ void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed
 double dmrg_reference(Ctx& c, int M0, int n_sweeps);
 double lcc_sweeps(Ctx& c, int M1, int n_sweeps);
 void compute_e3(Ctx& c);
+void compute_energies(Ctx& c);
 
 }  // namespace mpslcc

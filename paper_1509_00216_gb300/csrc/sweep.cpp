@@ -361,7 +361,7 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     }
     gt.push_back(t);
   }
-  run_gemms(c, gt);
+  run_gemm_tasks(c, gt);
   // FP64 eigendecompositions (cuSOLVER), eigenvalues ascending.  The
   // sectors are independent: they run concurrently on NEIG side streams,
   // largest first, each stream with its own handle and workspace.
@@ -478,7 +478,7 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     ct.push_back(g);
     io += (long)nd[i] * kq;
   }
-  run_gemms(c, ct);
+  run_gemm_tasks(c, ct);
   if (moving_right) {
     set_site_lf(c, m, l, std::move(iso));
     set_site_rf(c, m, l + 1, std::move(cen));
@@ -499,6 +499,14 @@ void invalidate_site(Family& F, int p) {
   for (int b = p + 1; b <= k; ++b) F.L[b].data.release();
   for (int b = 1; b <= p; ++b) F.R[b].data.release();
 }
+
+// Sets the precision of the per-site GEMM tasks for a scope.
+struct GemmPrec {
+  Ctx& c;
+  int saved;
+  GemmPrec(Ctx& c_, int p) : c(c_), saved(c_.gemm_prec) { c.gemm_prec = p; }
+  ~GemmPrec() { c.gemm_prec = saved; }
+};
 
 void bind(Ctx& c, Family& F, MPS* bra, int mpo, MPS* ket) {
   F.bra = bra;
@@ -623,10 +631,14 @@ void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed
 // ---------------------------------------------------------------------------
 double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
   int k = c.k;
+  const bool mixed = c.opts.prec != MPSLCC_FP64;
   init_random_mps(c, c.phi0, std::min(M0, 16), true, c.opts.seed);
-  bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
   double E = 0;
   bool all_conv = true;
+  {
+  // mixed precision: every per-site product on the tensor cores (split BF16)
+  GemmPrec gp(c, mixed ? MPSLCC_BF16X3 : MPSLCC_FP64);
+  bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
   for (int sw = 0; sw < n_sweeps; ++sw) {
     for (int dir = 0; dir < 2; ++dir) {
       bool right = dir == 0;
@@ -641,16 +653,10 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
         form_two_site(c, c.phi0, l, x.d());
         sigma_diag(c, P, dg.d());
         bool conv = false;
-        // low-precision products (split BF16 in mixed mode) for the search;
-        // the reported energy is an FP64 Rayleigh quotient at the last position
-        const int dprec = c.opts.prec == MPSLCC_FP64 ? MPSLCC_FP64 : MPSLCC_BF16X3;
-        const bool last = sw == n_sweeps - 1 && !right && l == 0;
+        const int dprec = mixed ? MPSLCC_BF16X3 : MPSLCC_FP64;
         // split-BF16 products reach a residual of ~2^-16 |H_eff|: stop there
-        double dtol = dprec == MPSLCC_FP64 ? std::max(c.opts.tol, 1e-13) : std::max(c.opts.tol, 1e-4);
+        double dtol = mixed ? std::max(c.opts.tol, 1e-4) : std::max(c.opts.tol, 1e-13);
         E = davidson(c, P, x.d(), n, dg.d(), dtol, c.opts.max_iter, c.opts.davidson_max_subspace, &conv, dprec);
-        if (dprec != MPSLCC_FP64 && last)  // FP64 polish of the reported eigenpair
-          E = davidson(c, P, x.d(), n, dg.d(), std::max(c.opts.tol, 1e-13), c.opts.max_iter,
-                       c.opts.davidson_max_subspace, &conv, MPSLCC_FP64);
         all_conv &= conv;
         double disc = truncate(c, c.phi0, l, x.d(), M0, right);
         c.max_disc = std::max(c.max_disc, disc);
@@ -662,6 +668,28 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
           fprintf(stderr, "[dmrg] sweep %d %s l=%d n=%ld E=%.12f disc=%.2e\n", sw, right ? "R" : "L", l, n, E, disc);
       }
     }
+  }
+  }
+  if (mixed) {
+    // FP64 pass: environments rebuilt in FP64 from the right and a final
+    // FP64 Davidson at position 0; E0 is that eigenvalue
+    bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
+    SigmaPlan P;
+    make_sigma_plan(c, c.f00, 0, P);
+    long n = P.nk;
+    DBuf x, dg;
+    x.alloc(&c, std::max(n, 1L) * sizeof(double));
+    dg.alloc(&c, std::max(n, 1L) * sizeof(double));
+    form_two_site(c, c.phi0, 0, x.d());
+    sigma_diag(c, P, dg.d());
+    bool conv = false;
+    E = davidson(c, P, x.d(), n, dg.d(), std::max(c.opts.tol, 1e-13), c.opts.max_iter, c.opts.davidson_max_subspace,
+                 &conv, MPSLCC_FP64);
+    all_conv &= conv;
+    truncate(c, c.phi0, 0, x.d(), M0, false);
+    invalidate_site(c.f00, 0);
+    invalidate_site(c.f00, 1);
+    env_update_right(c, c.f00, 1, P.rf);
   }
   c.E0 = E;
   c.have_E0 = true;
@@ -679,9 +707,13 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
     bind(c, c.s10, &c.phi1, MPO_ID, &c.phi0);
   }
   c.e3_valid = false;
+  c.e_valid = false;
   c.u11.L.clear();
   c.h11.L.clear();
   int prec = c.opts.prec;
+  const bool mixed = prec != MPSLCC_FP64;
+  GemmPrec gp(c, mixed ? MPSLCC_BF16X3 : MPSLCC_FP64);
+  const int rprec = mixed ? MPSLCC_BF16X3 : MPSLCC_FP64;
   double J = 0, E2 = 0;
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
@@ -712,8 +744,8 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
         dg.alloc(&c, std::max(n, 1L) * sizeof(double));
         p0.alloc(&c, std::max(n0, 1L) * sizeof(double));
         form_two_site(c, c.phi0, l, p0.d());
-        sigma_apply(c, P10, p0.d(), sb.d(), MPSLCC_FP64);   // P1^T H Phi0
-        sigma_apply(c, PS, p0.d(), ub.d(), MPSLCC_FP64);    // v = P1^T Phi0
+        sigma_apply(c, P10, p0.d(), sb.d(), rprec);   // P1^T H Phi0
+        sigma_apply(c, PS, p0.d(), ub.d(), rprec);    // v = P1^T Phi0
         // b = -(P1^T H Phi0 - E0 v), then project out v
         copyv(c, bb.d(), ub.d(), n);
         launch_axpby(n, -1.0, sb.d(), c.E0, bb.d(), c.s());
@@ -757,14 +789,11 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
             launch_axpy(n, 1.0, dx.d(), xb.d(), c.s());
           }
         }
-        // Hylleraas value J = x.Ax - 2 x.b; with FP64 products at the last
-        // position of the sweep (the reported E2), otherwise in the solve's
-        // residual precision
+        // local Hylleraas value J = x.Ax - 2 x.b in the sweep's precision (the
+        // FP64 value of the final state comes from mpslcc_energy)
         Vec ax;
         ax.alloc(c, n);
-        const bool last = (sw == n_sweeps - 1) && !right && l == 0;
-        const int jprec = (prec == MPSLCC_FP64 || last) ? MPSLCC_FP64 : MPSLCC_BF16X3;
-        A.apply(c, xb.d(), ax.d(), jprec);
+        A.apply(c, xb.d(), ax.d(), rprec);
         J = dev_dot(c, xb.d(), ax.d(), n) - 2.0 * dev_dot(c, xb.d(), bb.d(), n);
         E2 = J;
         delete tsol;
@@ -809,37 +838,48 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
   c.J = J;
   c.E2 = E2;
   c.have_E2 = true;
-  // overlap and norm at position 0 (Phi1's centre after the left pass)
-  {
-    SigmaPlan PS;
-    make_sigma_plan(c, c.s10, 0, PS);
-    DBuf x, p0, v;
-    x.alloc(&c, std::max(PS.nb, 1L) * sizeof(double));
-    v.alloc(&c, std::max(PS.nb, 1L) * sizeof(double));
-    p0.alloc(&c, std::max(PS.nk, 1L) * sizeof(double));
-    form_two_site(c, c.phi1, 0, x.d());
-    form_two_site(c, c.phi0, 0, p0.d());
-    sigma_apply(c, PS, p0.d(), v.d(), MPSLCC_FP64);
-    c.ovl01 = dev_dot(c, x.d(), v.d(), PS.nb);
-    c.norm1 = dev_dot(c, x.d(), x.d(), PS.nb);
-  }
   return E2;
 }
 
-void compute_e3(Ctx& c) {
-  MPSLCC_REQUIRE(c.phi1.present, ST_STATE, "E3 needs the first-order state");
-  bind(c, c.u11, &c.phi1, MPO_U, &c.phi1);
+// <bra|O|ket> in FP64 from freshly built FP64 environments, contracted at
+// position 0 (both MPS centred on their first site).
+double expect_fp64(Ctx& c, MPS* bra, int mpo, MPS* ket) {
+  GemmPrec gp(c, MPSLCC_FP64);
+  Family F;
+  bind(c, F, bra, mpo, ket);
   SigmaPlan P;
-  make_sigma_plan(c, c.u11, 0, P);
-  DBuf x, y;
-  x.alloc(&c, std::max(P.nb, 1L) * sizeof(double));
+  make_sigma_plan(c, F, 0, P);
+  DBuf xb, xk, y;
+  xb.alloc(&c, std::max(P.nb, 1L) * sizeof(double));
+  xk.alloc(&c, std::max(P.nk, 1L) * sizeof(double));
   y.alloc(&c, std::max(P.nb, 1L) * sizeof(double));
-  form_two_site(c, c.phi1, 0, x.d());
-  sigma_apply(c, P, x.d(), y.d(), MPSLCC_FP64);
-  c.E3 = dev_dot(c, x.d(), y.d(), P.nb);
-  c.e3_valid = true;
-  c.u11.L.clear();
-  c.u11.R.clear();
+  form_two_site(c, *bra, 0, xb.d());
+  form_two_site(c, *ket, 0, xk.d());
+  sigma_apply(c, P, xk.d(), y.d(), MPSLCC_FP64);
+  return dev_dot(c, xb.d(), y.d(), P.nb);
 }
+
+// FP64 energies of the current first-order state (Eq. 1b, Eq. 2 with n = 1):
+// with s = <Phi1|Phi0>, Q Phi1 = Phi1 - s Phi0 and b = -Q H Phi0,
+//   J = <QPhi1|(H0 - E0)|QPhi1> - 2<QPhi1|b>
+//     = <1|H0|1> - E0 <1|1> - 2 s (<1|H0|0> - E0 s) + 2 (<1|H|0> - s E0),
+// and E3 = <Phi1|U|Phi1>.
+void compute_energies(Ctx& c) {
+  MPSLCC_REQUIRE(c.phi1.present && c.phi0.present, ST_STATE, "energies need Phi0 and Phi1");
+  double A = expect_fp64(c, &c.phi1, MPO_H0, &c.phi1);
+  double N1 = expect_fp64(c, &c.phi1, MPO_ID, &c.phi1);
+  double s = expect_fp64(c, &c.phi1, MPO_ID, &c.phi0);
+  double g = expect_fp64(c, &c.phi1, MPO_H, &c.phi0);
+  double h = expect_fp64(c, &c.phi1, MPO_H0, &c.phi0);
+  c.J = A - c.E0 * N1 - 2.0 * s * (h - c.E0 * s) + 2.0 * (g - s * c.E0);
+  c.E2 = c.J;
+  c.ovl01 = s;
+  c.norm1 = N1;
+  c.E3 = expect_fp64(c, &c.phi1, MPO_U, &c.phi1);
+  c.e3_valid = true;
+  c.e_valid = true;
+}
+
+void compute_e3(Ctx& c) { compute_energies(c); }
 
 }  // namespace mpslcc

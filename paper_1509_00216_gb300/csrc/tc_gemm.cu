@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -24,8 +25,10 @@
 namespace mpslcc {
 
 struct alignas(64) TcTask {
-  CUtensorMap ma;       // A: rows x K, K contiguous
-  CUtensorMap mb;       // B: rows x K, K contiguous
+  CUtensorMap ma;       // A: rows x K, K contiguous (hi part in split mode)
+  CUtensorMap mb;       // B: rows x K, K contiguous (hi part in split mode)
+  CUtensorMap ma2;      // split mode: lo parts of A and B
+  CUtensorMap mb2;
   void* C;
   long long bstride;    // output offset between row batches (elements)
   int rpb;              // rows per batch of the output remap
@@ -35,8 +38,10 @@ struct alignas(64) TcTask {
   int ntile;            // UMMA N (multiple of 16, <= 256)
   int tm, tn;
   int mode;             // 0: FP32 atomic add, 1: BF16 store, 2: FP32 store,
-                        // 3: split BF16 store (hi at +0, lo at +soff, hi at +2 soff)
+                        // 3: split BF16 store (hi at +0, lo at +soff), 4: FP64 alpha/beta store
+  int split;            // operands are hi + lo pairs: acc += Ah Bh + Ah Bl + Al Bh
   long long soff;
+  double alpha, beta;   // mode 4: FP64 store C = alpha acc + beta C
   long long tile0;
 };
 
@@ -170,21 +175,24 @@ __device__ __forceinline__ int find_tc(const TcTask* t, int n, long long tile) {
   return lo;
 }
 
-template <int PREC>
+template <int PREC, bool SPLIT>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
                                                           long long total, int* err) {
   extern __shared__ uint8_t smem_raw[];
+  // split mode keeps hi and lo tiles of both operands: half as many stages
+  constexpr int NST = SPLIT ? STAGES / 2 : STAGES;
+  constexpr int SB = SPLIT ? 2 * STAGE_BYTES : STAGE_BYTES;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
+  uint64_t* empty = full + NST;
+  uint64_t* done = empty + NST;
   volatile uint32_t* tslot = (volatile uint32_t*)(done + 1);
   volatile int* s_abort = (volatile int*)(tslot + 1);
   constexpr int KT = PREC == MPSLCC_BF16 ? 64 : 32;  // K elements per 128-byte row
   const int warp = threadIdx.x >> 5;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -221,23 +229,37 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restric
       // TMA producer
       const uint32_t bbytes = (uint32_t)ntile * 128u;
       for (int j = 0; j < nk; ++j) {
-        const uint32_t s = (it + j) % STAGES, ph = ((it + j) / STAGES) & 1u;
+        const uint32_t s = (it + j) % NST, ph = ((it + j) / NST) & 1u;
         if (!mbar_wait(&empty[s], ph ^ 1u, err, 1)) { *s_abort = 1; break; }
-        mbar_expect_tx(&full[s], A_BYTES + bbytes);
-        tma_load_2d(smem + s * STAGE_BYTES, &T->ma, &full[s], (kt0 + j) * KT, row0);
-        tma_load_2d(smem + s * STAGE_BYTES + A_BYTES, &T->mb, &full[s], (kt0 + j) * KT, col0);
+        uint8_t* st = smem + s * SB;
+        mbar_expect_tx(&full[s], (SPLIT ? 2u : 1u) * (A_BYTES + bbytes));
+        tma_load_2d(st, &T->ma, &full[s], (kt0 + j) * KT, row0);
+        tma_load_2d(st + A_BYTES, &T->mb, &full[s], (kt0 + j) * KT, col0);
+        if (SPLIT) {
+          tma_load_2d(st + STAGE_BYTES, &T->ma2, &full[s], (kt0 + j) * KT, row0);
+          tma_load_2d(st + STAGE_BYTES + A_BYTES, &T->mb2, &full[s], (kt0 + j) * KT, col0);
+        }
       }
     } else if (threadIdx.x == 32) {
       // MMA issuer
       const uint32_t id = idesc<PREC>(128, ntile);
       for (int j = 0; j < nk; ++j) {
-        const uint32_t s = (it + j) % STAGES, ph = ((it + j) / STAGES) & 1u;
+        const uint32_t s = (it + j) % NST, ph = ((it + j) / NST) & 1u;
         if (!mbar_wait(&full[s], ph, err, 2)) { *s_abort = 1; break; }
         fence_after();
-        const uint64_t a = sdesc(smem + s * STAGE_BYTES);
-        const uint64_t b = sdesc(smem + s * STAGE_BYTES + A_BYTES);
+        uint8_t* st = smem + s * SB;
+        const uint64_t a = sdesc(st);
+        const uint64_t b = sdesc(st + A_BYTES);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) umma<PREC>(tmem, a + 2 * kk, b + 2 * kk, id, (j > 0 || kk > 0) ? 1u : 0u);
+        if (SPLIT) {
+          const uint64_t a2 = sdesc(st + STAGE_BYTES);
+          const uint64_t b2 = sdesc(st + STAGE_BYTES + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) umma<PREC>(tmem, a + 2 * kk, b2 + 2 * kk, id, 1u);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) umma<PREC>(tmem, a2 + 2 * kk, b + 2 * kk, id, 1u);
+        }
         umma_commit(&empty[s]);
       }
       umma_commit(done);
@@ -279,12 +301,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restric
             for (int q = 0; q < 4; ++q) d0[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
             if (T->mode == 3) {
               uint4* d1 = reinterpret_cast<uint4*>(C + T->soff);
-              uint4* d2 = reinterpret_cast<uint4*>(C + 2 * T->soff);
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                d1[q] = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
-                d2[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
-              }
+              for (int q = 0; q < 4; ++q) d1[q] = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
             }
             continue;
           }
@@ -297,6 +315,14 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restric
                                __uint_as_float(v[4 * q + 3]));
           continue;
         }
+        if (T->mode == 4) {
+          double* C = (double*)T->C + roff + c0;
+          if (T->beta == 0.0)
+            for (int j = 0; j < nv; ++j) C[j] = T->alpha * (double)__uint_as_float(v[j]);
+          else
+            for (int j = 0; j < nv; ++j) C[j] = T->alpha * (double)__uint_as_float(v[j]) + T->beta * C[j];
+          continue;
+        }
         if (T->mode == 0) {
           float* C = (float*)T->C + roff + c0;
           for (int j = 0; j < nv; ++j) atomicAdd(C + j, __uint_as_float(v[j]));
@@ -304,7 +330,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restric
           __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
           for (int j = 0; j < nv; ++j) C[j] = __float2bfloat16_rn(__uint_as_float(v[j]));
         } else if (T->mode == 3) {
-          // two-term BF16 split of the FP32 result: [hi | lo | hi]
+          // two-term BF16 split of the FP32 result: [hi | lo]
           __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
           for (int j = 0; j < nv; ++j) {
             const float f = __uint_as_float(v[j]);
@@ -312,7 +338,6 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restric
             const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
             C[j] = h;
             C[j + T->soff] = l;
-            C[j + 2 * T->soff] = h;
           }
         } else {
           float* C = (float*)T->C + roff + c0;
@@ -336,8 +361,11 @@ struct ConvTask {
   void* dst;
   int rows, cols, src_ld, dst_ld, batch;
   long long s_src, s_dst;
-  int pattern;          // 0 plain; split BF16 into three column blocks
-  long long soff;       // 1: [hi | hi | lo], 2: [hi | lo | hi] at offsets 0, soff, 2 soff
+  int pattern;          // 0 plain; 1 split BF16: hi at +0, lo at +soff;
+                        // 2 / 3: three-piece split h, m, l written as six blocks at
+                        // +j soff, [h h m h m l] (A side) / [h m h l m h] (B side)
+  long long soff;
+  int trans;            // read the source transposed: dst(r, c) = src[c * src_ld + r]
   long long tile0;
 };
 constexpr int CONV_CHUNK = 4096;
@@ -359,20 +387,38 @@ __global__ void conv_kernel(const ConvTask* __restrict__ t, int ntasks, long lon
     const long long ch = local - (long long)b * per;
     const long long e1 = min(nel, (ch + 1) * CONV_CHUNK);
     for (long long e = ch * CONV_CHUNK + threadIdx.x; e < e1; e += blockDim.x) {
-      const int rr = (int)(e / T.cols), cc = (int)(e - (long long)rr * T.cols);
-      const double v = T.src[b * T.s_src + (long long)rr * T.src_ld + cc];
+      int rr, cc;
+      double v;
+      if (T.trans) {  // consecutive threads walk the source row (coalesced reads)
+        cc = (int)(e / T.rows);
+        rr = (int)(e - (long long)cc * T.rows);
+        v = T.src[b * T.s_src + (long long)cc * T.src_ld + rr];
+      } else {
+        rr = (int)(e / T.cols);
+        cc = (int)(e - (long long)rr * T.cols);
+        v = T.src[b * T.s_src + (long long)rr * T.src_ld + cc];
+      }
       const long long o = b * T.s_dst + (long long)rr * T.dst_ld + cc;
       if (PREC == MPSLCC_TF32) {
         ((float*)T.dst)[o] = (float)v;
       } else if (T.pattern == 0) {
         ((__nv_bfloat16*)T.dst)[o] = __float2bfloat16_rn((float)v);
-      } else {
+      } else if (T.pattern == 1) {
         __nv_bfloat16* d = (__nv_bfloat16*)T.dst + o;
         const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
         const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
         d[0] = h;
-        d[T.soff] = T.pattern == 1 ? h : l;
-        d[2 * T.soff] = T.pattern == 1 ? l : h;
+        d[T.soff] = l;
+      } else {
+        __nv_bfloat16* d = (__nv_bfloat16*)T.dst + o;
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+        const double r1 = v - (double)__bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
+        const __nv_bfloat16 l = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(m)));
+        const __nv_bfloat16 pa[6] = {h, h, m, h, m, l}, pb[6] = {h, m, h, l, m, h};
+        const __nv_bfloat16* pp = T.pattern == 2 ? pa : pb;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) d[j * T.soff] = pp[j];
       }
     }
   }
@@ -428,15 +474,24 @@ int sm_count(Ctx& c) {
   return n > 0 ? n : 148;
 }
 
-// C (m x n, remapped rows) op= A (m x K) B (n x K)^T
+// C (m x n, remapped rows) op= A (m x K) B (n x K)^T.  In split mode (prec
+// BF16X3) each operand row holds the hi part at +0 and the lo part at +lo_off
+// elements (lda / ldb span both); k is the length of one part.
 TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long ldb, int m, int n, int k, void* C,
-                 int ldc, int rpb, long long bstride, int mode, int ksplit_hint, long long soff = 0) {
+                 int ldc, int rpb, long long bstride, int mode, int ksplit_hint, long long soff = 0,
+                 long lo_off = 0) {
   TcTask t;
   std::memset(&t, 0, sizeof(t));
   const int KT = prec == MPSLCC_TF32 ? 32 : 64;
   t.ntile = (int)std::min<long>(256, (n + 15) / 16 * 16);
   encode_map(c, &t.ma, prec, A, m, k, lda, 128);
   encode_map(c, &t.mb, prec, B, n, k, ldb, t.ntile);
+  t.split = prec == MPSLCC_BF16X3;
+  if (t.split) {
+    MPSLCC_REQUIRE(lo_off >= k && lo_off % 8 == 0, ST_INTERNAL, "bad split operand layout");
+    encode_map(c, &t.ma2, prec, (const char*)A + lo_off * 2, m, k, lda, 128);
+    encode_map(c, &t.mb2, prec, (const char*)B + lo_off * 2, n, k, ldb, t.ntile);
+  }
   t.C = C;
   t.ldc = ldc;
   t.rpb = rpb;
@@ -452,13 +507,13 @@ TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long 
   t.tm = (m + 127) / 128;
   t.tn = (n + t.ntile - 1) / t.ntile;
   // output range check
-  const int es = (mode == 1 || mode == 3) ? 2 : 4;
+  const int es = (mode == 1 || mode == 3) ? 2 : (mode == 4 ? 8 : 4);
   long long last = (long long)((m - 1) / rpb) * bstride + (long long)((m - 1) % rpb) * ldc + (n - 1);
   for (int r = 0; r < std::min(m, rpb); ++r) {
     long long l2 = (long long)((m - 1 - r) / rpb) * bstride + (long long)((m - 1 - r) % rpb) * ldc + (n - 1);
     last = std::max(last, l2);
   }
-  if (mode == 3) last += 2 * soff;
+  if (mode == 3) last += soff;
   t.soff = soff;
   c.check_bytes(C, (last + 1) * es, "tc output");
   return t;
@@ -473,28 +528,28 @@ long long plan_tc(std::vector<TcTask>& t) {
   return tot;
 }
 
+template <int P, bool S>
+void launch_variant(cudaStream_t st, int grid, const TcTask* d_tasks, int ntasks, long long total, int* err) {
+  static bool attr = false;
+  if (!attr) {
+    cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
+               "smem attr");
+    attr = true;
+  }
+  tc_gemm_kernel<P, S><<<grid, 128, SMEM_BYTES, st>>>(d_tasks, ntasks, total, err);
+}
+
+void launch_tc_stream(cudaStream_t st, int grid, int prec, const TcTask* d_tasks, int ntasks, long long total,
+                      int* err) {
+  if (prec == MPSLCC_BF16X3) launch_variant<MPSLCC_BF16, true>(st, grid, d_tasks, ntasks, total, err);
+  else if (prec == MPSLCC_BF16) launch_variant<MPSLCC_BF16, false>(st, grid, d_tasks, ntasks, total, err);
+  else launch_variant<MPSLCC_TF32, false>(st, grid, d_tasks, ntasks, total, err);
+}
+
 void launch_tc(Ctx& c, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err) {
   if (total <= 0 || ntasks <= 0) return;
   int grid = (int)std::min<long long>(total, (long long)sm_count(c));
-  if (kprec(prec) == MPSLCC_BF16) {
-    static bool attr = false;
-    if (!attr) {
-      cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<MPSLCC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      SMEM_BYTES),
-                 "smem attr");
-      attr = true;
-    }
-    tc_gemm_kernel<MPSLCC_BF16><<<grid, 128, SMEM_BYTES, c.s()>>>(d_tasks, ntasks, total, err);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<MPSLCC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      SMEM_BYTES),
-                 "smem attr");
-      attr = true;
-    }
-    tc_gemm_kernel<MPSLCC_TF32><<<grid, 128, SMEM_BYTES, c.s()>>>(d_tasks, ntasks, total, err);
-  }
+  launch_tc_stream(c.s(), grid, prec, d_tasks, ntasks, total, err);
   cuda_check(cudaGetLastError(), "tc_gemm launch");
   c.st.kernel_launches++;
   c.st.gemm_launches++;
@@ -505,9 +560,16 @@ void run_conv(Ctx& c, int prec, std::vector<ConvTask>& t, DBuf& dtasks) {
   long long tot = 0;
   const int es = esize(prec);
   for (auto& x : t) {
-    c.check_range(x.src, 0, (long long)(x.batch - 1) * x.s_src + (long long)(x.rows - 1) * x.src_ld + x.cols - 1,
-                  "conv src");
-    c.check_bytes(x.dst, ((long long)(x.batch - 1) * x.s_dst + (long long)(x.rows - 1) * x.dst_ld + x.cols) * es,
+    if (x.trans)
+      c.check_range(x.src, 0, (long long)(x.batch - 1) * x.s_src + (long long)(x.cols - 1) * x.src_ld + x.rows - 1,
+                    "conv src");
+    else
+      c.check_range(x.src, 0, (long long)(x.batch - 1) * x.s_src + (long long)(x.rows - 1) * x.src_ld + x.cols - 1,
+                    "conv src");
+    const long long blocks = x.pattern == 0 ? 0 : (x.pattern == 1 ? 1 : 5);  // extra split blocks
+    c.check_bytes(x.dst,
+                  ((long long)(x.batch - 1) * x.s_dst + (long long)(x.rows - 1) * x.dst_ld + blocks * x.soff + x.cols) *
+                      es,
                   "conv dst");
     x.tile0 = tot;
     long long nel = (long long)x.rows * x.cols;
@@ -563,9 +625,9 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   P.tc = S;
   S->prec = prec;
   const int es = esize(prec);
-  // split mode: operands stored as three K blocks so that one product over
-  // 3K accumulates hi*hi + hi*lo + lo*hi (A blocks [hi|hi|lo], B [hi|lo|hi])
-  const int sp = prec == MPSLCC_BF16X3 ? 3 : 1;
+  // split mode: every operand row stores its BF16 hi part, then its lo part
+  // (K blocks [hi | lo]); the kernel accumulates hi*hi + hi*lo + lo*hi
+  const int sp = prec == MPSLCC_BF16X3 ? 2 : 1;
   const LeftFused& lf = P.lf;
   const RightFused& rf = P.rf;
   const size_t nbk = P.mid_b.size(), nkk = P.mid_k.size();
@@ -627,7 +689,7 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
       t.batch = sg.nw;
       t.s_src = sg.width;
       t.s_dst = pad8(sg.width);
-      t.pattern = sp == 3 ? 1 : 0;
+      t.pattern = sp == 2 ? 1 : 0;
       t.soff = S->K8[bi];
       cv.push_back(t);
     }
@@ -644,7 +706,7 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     t.src_ld = rk;
     t.dst_ld = (int)(sp * pad8(rk));
     t.batch = 1;
-    t.pattern = sp == 3 ? 1 : 0;
+    t.pattern = sp == 2 ? 1 : 0;
     t.soff = pad8(rk);
     cv.push_back(t);
   }
@@ -661,12 +723,12 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     t.src_ld = t.cols;
     t.dst_ld = (int)(sp * pad8(t.cols));
     t.batch = 1;
-    t.pattern = sp == 3 ? 2 : 0;
+    t.pattern = sp == 2 ? 1 : 0;
     t.soff = pad8(t.cols);
     S->xconv.push_back(t);
   }
   // phase 1: T_w^T = R'_w psi^T for all channels of a class in one tall GEMM
-  const int mode1 = sp == 3 ? 3 : (prec == MPSLCC_TF32 ? 2 : 1);
+  const int mode1 = sp == 2 ? 3 : (prec == MPSLCC_TF32 ? 2 : 1);
   std::vector<TcTask> t1, t2;
   for (size_t si = 0; si < rf.stk.size(); ++si) {
     const auto& st = rf.stk[si];
@@ -677,8 +739,10 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     long kk = sp * pad8(rk);
     void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + koff8[bi][g]) * es;
     t1.push_back(make_task(c, prec, (char*)S->rstk.p + (size_t)S->stk_off[si] * es, kk,
-                           (char*)S->x.p + (size_t)S->x_off[ki] * es, kk, st.nw * rb, lk, (int)kk, C,
-                           (int)(sp * S->K8[bi]), rb, pad8(lk), mode1, 1, S->K8[bi]));
+                           (char*)S->x.p + (size_t)S->x_off[ki] * es, kk, st.nw * rb, lk,
+                           (int)(sp == 2 ? rk : kk), C, (int)(sp * S->K8[bi]), rb, pad8(lk), mode1, 1, S->K8[bi],
+                           pad8(rk)));
+    // algorithmic bytes: operands and result once (hi + lo parts in split mode)
     S->bytes1 += (double)es * sp * ((double)st.nw * rb * rk + (double)lk * rk + (double)st.nw * rb * lk);
   }
   // phase 2: sigma = Lcat Tt^T, split over K
@@ -694,9 +758,9 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     long KK = sp * S->K8[bi];
     int ks = (int)std::max(1LL, (target + base - 1) / std::max(1LL, base));
     t2.push_back(make_task(c, prec, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, KK,
-                           (char*)S->tt.p + (size_t)S->tt_off[bi] * es, KK, lb, rb, (int)KK,
-                           (float*)S->y.p + P.off_b[bi], rb, 1 << 30, 0, 0, ks));
-    S->bytes2 += (double)es * ((double)lb * KK + (double)rb * KK) + 4.0 * lb * rb;
+                           (char*)S->tt.p + (size_t)S->tt_off[bi] * es, KK, lb, rb, (int)S->K8[bi],
+                           (float*)S->y.p + P.off_b[bi], rb, 1 << 30, 0, 0, ks, 0, S->K8[bi]));
+    S->bytes2 += (double)es * sp * ((double)lb * S->K8[bi] + (double)rb * S->K8[bi]) + 4.0 * lb * rb;
   }
   S->n1 = (int)t1.size();
   S->n2 = (int)t2.size();
@@ -746,7 +810,7 @@ void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
 void tc_selftest(Ctx& c, int prec, int m, int n, int k, const double* A, const double* B, double* C, int mode,
                  int ksplit) {
   const int es = esize(prec);
-  const int sp = prec == MPSLCC_BF16X3 ? 3 : 1;
+  const int sp = prec == MPSLCC_BF16X3 ? 2 : 1;
   long k8 = pad8(k), kk = sp * k8;
   DBuf dA, dB, lA, lB, out, err, conv;
   dA.alloc(&c, std::max<long>((long)m * k, 1) * 8);
@@ -760,16 +824,17 @@ void tc_selftest(Ctx& c, int prec, int m, int n, int k, const double* A, const d
   std::vector<ConvTask> cv(2);
   std::memset(cv.data(), 0, sizeof(ConvTask) * 2);
   cv[0].src = dA.d(); cv[0].dst = lA.p; cv[0].rows = m; cv[0].cols = k; cv[0].src_ld = k; cv[0].dst_ld = (int)kk;
-  cv[0].batch = 1; cv[0].pattern = sp == 3 ? 1 : 0; cv[0].soff = k8;
+  cv[0].batch = 1; cv[0].pattern = sp == 2 ? 1 : 0; cv[0].soff = k8;
   cv[1].src = dB.d(); cv[1].dst = lB.p; cv[1].rows = n; cv[1].cols = k; cv[1].src_ld = k; cv[1].dst_ld = (int)kk;
-  cv[1].batch = 1; cv[1].pattern = sp == 3 ? 2 : 0; cv[1].soff = k8;
+  cv[1].batch = 1; cv[1].pattern = sp == 2 ? 1 : 0; cv[1].soff = k8;
   run_conv(c, prec, cv, conv);
   const int oes = mode == 1 ? 2 : 4;
   out.alloc(&c, (size_t)m * n * oes);
   cuda_check(cudaMemsetAsync(out.p, 0, (size_t)m * n * oes, c.s()), "z");
   err.alloc(&c, 16);
   cuda_check(cudaMemsetAsync(err.p, 0, 16, c.s()), "z");
-  std::vector<TcTask> t{make_task(c, prec, lA.p, kk, lB.p, kk, m, n, (int)kk, out.p, n, 1 << 30, 0, mode, ksplit)};
+  std::vector<TcTask> t{make_task(c, prec, lA.p, kk, lB.p, kk, m, n, (int)(sp == 2 ? k8 : kk), out.p, n, 1 << 30,
+                                  0, mode, ksplit, 0, k8)};
   long long tiles = plan_tc(t);
   DBuf dt;
   dt.alloc(&c, sizeof(TcTask));
@@ -846,7 +911,7 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
   MPSLCC_REQUIRE(prec >= MPSLCC_TF32 && prec <= MPSLCC_BF16X3, ST_ARG, "prec must be TF32, BF16 or BF16X3");
   MPSLCC_REQUIRE(m >= 1 && n >= 1 && k >= 1 && dA && dB && dC, ST_ARG, "bad argument");
   const int es = esize(prec);
-  const int sp = prec == MPSLCC_BF16X3 ? 3 : 1;
+  const int sp = prec == MPSLCC_BF16X3 ? 2 : 1;
   const long k8 = pad8(k), kk = sp * k8;
   // scratch layout: [conv tasks | tc task | error flag | A copy | B copy | FP32 result]
   const size_t o_conv = 0, o_task = up256(2 * sizeof(ConvTask)), o_err = o_task + up256(sizeof(TcTask));
@@ -865,9 +930,9 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
   ConvTask cv[2];
   std::memset(cv, 0, sizeof(cv));
   cv[0].src = dA; cv[0].dst = base + o_a; cv[0].rows = m; cv[0].cols = k; cv[0].src_ld = k; cv[0].dst_ld = (int)kk;
-  cv[0].batch = 1; cv[0].pattern = sp == 3 ? 1 : 0; cv[0].soff = k8;
+  cv[0].batch = 1; cv[0].pattern = sp == 2 ? 1 : 0; cv[0].soff = k8;
   cv[1].src = dB; cv[1].dst = base + o_b; cv[1].rows = n; cv[1].cols = k; cv[1].src_ld = k; cv[1].dst_ld = (int)kk;
-  cv[1].batch = 1; cv[1].pattern = sp == 3 ? 2 : 0; cv[1].soff = k8;
+  cv[1].batch = 1; cv[1].pattern = sp == 2 ? 1 : 0; cv[1].soff = k8;
   long long tot = 0;
   for (auto& x : cv) {
     x.tile0 = tot;
@@ -883,16 +948,22 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
   std::memset(&t, 0, sizeof(t));
   const int KT = prec == MPSLCC_TF32 ? 32 : 64;
   t.ntile = (int)std::min<long>(256, (n + 15) / 16 * 16);
-  noalloc_map(&t.ma, prec, base + o_a, m, kk, kk, 128);
-  noalloc_map(&t.mb, prec, base + o_b, n, kk, kk, t.ntile);
+  const long klen = sp == 2 ? k8 : kk;  // length of one operand part along K
+  noalloc_map(&t.ma, prec, base + o_a, m, klen, kk, 128);
+  noalloc_map(&t.mb, prec, base + o_b, n, klen, kk, t.ntile);
+  t.split = sp == 2;
+  if (t.split) {
+    noalloc_map(&t.ma2, prec, base + o_a + k8 * 2, m, klen, kk, 128);
+    noalloc_map(&t.mb2, prec, base + o_b + k8 * 2, n, klen, kk, t.ntile);
+  }
   t.C = base + o_c;
   t.ldc = n;
   t.rpb = 1 << 30;
   t.m = m;
   t.n = n;
-  t.k = (int)kk;
+  t.k = (int)klen;
   t.mode = 2;
-  t.ksteps = (int)((kk + KT - 1) / KT);
+  t.ksteps = (int)((klen + KT - 1) / KT);
   t.ksplit = 1;
   t.kchunk = t.ksteps;
   t.tm = (m + 127) / 128;
@@ -901,17 +972,7 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
   long long tiles = (long long)t.tm * t.tn;
   cuda_check(cudaMemcpyAsync(base + o_task, &t, sizeof(t), cudaMemcpyHostToDevice, stream), "noalloc task");
   int grid = (int)std::min<long long>(tiles, 148);
-  if (kprec(prec) == MPSLCC_BF16) {
-    cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<MPSLCC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    SMEM_BYTES), "smem attr");
-    tc_gemm_kernel<MPSLCC_BF16><<<grid, 128, SMEM_BYTES, stream>>>((const TcTask*)(base + o_task), 1, tiles,
-                                                                    (int*)(base + o_err));
-  } else {
-    cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<MPSLCC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    SMEM_BYTES), "smem attr");
-    tc_gemm_kernel<MPSLCC_TF32><<<grid, 128, SMEM_BYTES, stream>>>((const TcTask*)(base + o_task), 1, tiles,
-                                                                    (int*)(base + o_err));
-  }
+  launch_tc_stream(stream, grid, prec, (const TcTask*)(base + o_task), 1, tiles, (int*)(base + o_err));
   cuda_check(cudaGetLastError(), "noalloc gemm");
   launch_f32_to_f64((long)m * n, (const float*)(base + o_c), dC, stream);
   cuda_check(cudaGetLastError(), "noalloc result");
@@ -919,6 +980,96 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
   cuda_check(cudaMemcpyAsync(&h, base + o_err, sizeof(int), cudaMemcpyDeviceToHost, stream), "noalloc flag");
   cuda_check(cudaStreamSynchronize(stream), "noalloc sync");
   if (h) throw Error(ST_TIMEOUT, "tensor-core kernel gave up waiting on an mbarrier");
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GEMM tasks on the tensor cores.  Each operand is converted once into
+// a three-piece BF16 split v ~ h + m + l, laid out along K as six blocks so
+// that one BF16 product accumulates hh + hm + mh + hl + mm + lh in FP32
+// (K-major rows, transposed where the task reads the operand transposed;
+// operands shared by several tasks or batch entries are converted once).  The
+// epilogue writes C = alpha acc + beta C in FP64.  Relative accuracy ~2^-24
+// (FP32 accumulation), used for the environment, fusion and truncation
+// products of mixed-precision sweeps.
+// ---------------------------------------------------------------------------
+void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
+  if (tasks.empty()) return;
+  struct Key {
+    const double* p;
+    int rows, cols, ld, trans;
+    bool operator<(const Key& o) const {
+      if (p != o.p) return p < o.p;
+      if (rows != o.rows) return rows < o.rows;
+      if (cols != o.cols) return cols < o.cols;
+      if (ld != o.ld) return ld < o.ld;
+      return trans < o.trans;
+    }
+  };
+  std::map<Key, long> opoff;
+  std::vector<ConvTask> cv;
+  long tot = 0;
+  auto add_op = [&](const double* p, int rows, int cols, int ld, int trans, int side) -> long {
+    Key k{p, rows, cols, ld, trans + 2 * side};
+    auto it = opoff.find(k);
+    if (it != opoff.end()) return it->second;
+    long off = tot;
+    const long kp = pad8(cols);
+    tot += pad8((long)rows * 6 * kp);
+    ConvTask t;
+    std::memset(&t, 0, sizeof(t));
+    t.src = p;
+    t.dst = (void*)(uintptr_t)off;  // relocated below
+    t.rows = rows;
+    t.cols = cols;
+    t.src_ld = ld;
+    t.dst_ld = (int)(6 * kp);
+    t.batch = 1;
+    t.pattern = side;
+    t.soff = kp;
+    t.trans = trans;
+    cv.push_back(t);
+    opoff[k] = off;
+    return off;
+  };
+  struct Job { long ao, bo; double* C; int m, n, k, ldc; double alpha, beta; };
+  std::vector<Job> jobs;
+  for (const auto& t : tasks) {
+    if (t.m <= 0 || t.n <= 0 || t.batch <= 0) continue;
+    MPSLCC_REQUIRE(t.k > 0 && t.ksplit <= 1, ST_INTERNAL, "tensor-core FP64 task shape");
+    const bool ta = t.flags & GEMM_TA, tb = t.flags & GEMM_TB;
+    for (int b = 0; b < t.batch; ++b) {
+      const double* A = t.A + (long long)b * t.sA;
+      const double* B = t.B + (long long)b * t.sB;
+      long ao = add_op(A, t.m, t.k, t.lda, ta ? 1 : 0, 2);   // op(A): m x k
+      long bo = add_op(B, t.n, t.k, t.ldb, tb ? 0 : 1, 3);   // op(B)^T: n x k
+      jobs.push_back({ao, bo, t.C + (long long)b * t.sC, t.m, t.n, t.k, t.ldc, t.alpha, t.beta});
+    }
+  }
+  if (jobs.empty()) return;
+  c.scratch_tc.ensure(&c, std::max<long>(tot, 8) * 2);
+  cuda_check(cudaMemsetAsync(c.scratch_tc.p, 0, std::max<long>(tot, 8) * 2, c.s()), "tc scratch zero");
+  char* base = (char*)c.scratch_tc.p;
+  for (auto& t : cv) t.dst = base + (uintptr_t)t.dst * 2;
+  run_conv(c, MPSLCC_BF16, cv, c.tc_conv_tasks);
+  std::vector<TcTask> tt;
+  tt.reserve(jobs.size());
+  for (const auto& j : jobs) {
+    const long kp = pad8(j.k);
+    TcTask t = make_task(c, MPSLCC_BF16, base + j.ao * 2, 6 * kp, base + j.bo * 2, 6 * kp, j.m, j.n, (int)(6 * kp),
+                         j.C, j.ldc, 1 << 30, 0, 4, 1);
+    t.alpha = j.alpha;
+    t.beta = j.beta;
+    tt.push_back(t);
+  }
+  long long tiles = plan_tc(tt);
+  c.tc_gemm_tasks.ensure(&c, tt.size() * sizeof(TcTask));
+  cuda_check(cudaMemcpyAsync(c.tc_gemm_tasks.p, tt.data(), tt.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
+             "tc gemm tasks");
+  c.tc_err.ensure(&c, 16);
+  cuda_check(cudaMemsetAsync(c.tc_err.p, 0, 16, c.s()), "tc err zero");
+  launch_tc(c, MPSLCC_BF16, (const TcTask*)c.tc_gemm_tasks.p, (int)tt.size(), tiles, (int*)c.tc_err.p);
+  for (const auto& j : jobs) c.st.tc_gemm_flops += 2.0 * j.m * j.n * j.k;
+  check_err(c, c.tc_err);
 }
 
 }  // namespace mpslcc
