@@ -52,7 +52,9 @@ constexpr int A_BYTES = 128 * 128;           // 128 rows x 128 bytes
 constexpr int B_BYTES_MAX = 256 * 128;       // up to 256 rows x 128 bytes
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES_MAX;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int TMEM_COLS = 256;
+constexpr int ACC_COLS = 256;                // one FP32 accumulator (N <= 256)
+constexpr int TMEM_COLS = 2 * ACC_COLS;      // double-buffered
+constexpr int TC_THREADS = 192;              // TMA warp, MMA warp, 4 epilogue warps
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on every mbarrier wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -66,6 +68,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
@@ -175,32 +181,106 @@ __device__ __forceinline__ int find_tc(const TcTask* t, int n, long long tile) {
   return lo;
 }
 
+// Writes one accumulator row segment (32 FP32 values of row `roff`,
+// columns c0 .. c0 + nv - 1) in the task's output mode.
+__device__ __forceinline__ void store_row(const TcTask* T, long long roff, int c0, int nv, const uint32_t* v) {
+  if (T->mode == 1 || T->mode == 3) {
+    // BF16 rows: a thread owns 32 contiguous outputs = 64 bytes; store
+    // them as four 16-byte vectors when aligned
+    __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
+    if (nv == 32 && ((uintptr_t)C & 15) == 0 && (T->mode == 1 || (T->soff & 7) == 0)) {
+      uint32_t hi[16], lo[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(f0 - hf.x, f1 - hf.y);
+        hi[j] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[j] = *reinterpret_cast<const uint32_t*>(&l);
+      }
+      uint4* d0 = reinterpret_cast<uint4*>(C);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) d0[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
+      if (T->mode == 3) {
+        uint4* d1 = reinterpret_cast<uint4*>(C + T->soff);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d1[q] = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
+      }
+      return;
+    }
+  }
+  if (T->mode == 2 && nv == 32 && (((uintptr_t)((float*)T->C + roff + c0)) & 15) == 0) {
+    float4* d = reinterpret_cast<float4*>((float*)T->C + roff + c0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      d[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
+                         __uint_as_float(v[4 * q + 3]));
+    return;
+  }
+  if (T->mode == 4) {
+    double* C = (double*)T->C + roff + c0;
+    if (T->beta == 0.0)
+      for (int j = 0; j < nv; ++j) C[j] = T->alpha * (double)__uint_as_float(v[j]);
+    else
+      for (int j = 0; j < nv; ++j) C[j] = T->alpha * (double)__uint_as_float(v[j]) + T->beta * C[j];
+    return;
+  }
+  if (T->mode == 0) {
+    float* C = (float*)T->C + roff + c0;
+    for (int j = 0; j < nv; ++j) atomicAdd(C + j, __uint_as_float(v[j]));
+  } else if (T->mode == 1) {
+    __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
+    for (int j = 0; j < nv; ++j) C[j] = __float2bfloat16_rn(__uint_as_float(v[j]));
+  } else if (T->mode == 3) {
+    // two-term BF16 split of the FP32 result: [hi | lo]
+    __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
+    for (int j = 0; j < nv; ++j) {
+      const float f = __uint_as_float(v[j]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(f);
+      const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
+      C[j] = h;
+      C[j + T->soff] = l;
+    }
+  } else {
+    float* C = (float*)T->C + roff + c0;
+    for (int j = 0; j < nv; ++j) C[j] = __uint_as_float(v[j]);
+  }
+}
+
 template <int PREC, bool SPLIT>
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
-                                                          long long total, int* err) {
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
+                                                                 long long total, int* err) {
+  // Warp roles: warp 0 issues TMA, warp 1 issues MMA (and owns the tensor
+  // memory), warps 2..5 drain a double-buffered accumulator, so the loads and
+  // products of the next tile overlap the epilogue of the previous one.
   extern __shared__ uint8_t smem_raw[];
   // split mode keeps hi and lo tiles of both operands: half as many stages
   constexpr int NST = SPLIT ? STAGES / 2 : STAGES;
   constexpr int SB = SPLIT ? 2 * STAGE_BYTES : STAGE_BYTES;
+  constexpr int KT = PREC == MPSLCC_BF16 ? 64 : 32;  // K elements per 128-byte row
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
   uint64_t* empty = full + NST;
-  uint64_t* done = empty + NST;
-  volatile uint32_t* tslot = (volatile uint32_t*)(done + 1);
+  uint64_t* acc_full = empty + NST;      // [2]
+  uint64_t* acc_empty = acc_full + 2;    // [2]
+  volatile uint32_t* tslot = (volatile uint32_t*)(acc_empty + 2);
   volatile int* s_abort = (volatile int*)(tslot + 1);
-  constexpr int KT = PREC == MPSLCC_BF16 ? 64 : 32;  // K elements per 128-byte row
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+    }
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32((const void*)tslot)),
                  "r"(TMEM_COLS)
@@ -212,65 +292,92 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restric
   fence_after();
   const uint32_t tmem = *tslot;
 
-  uint32_t it = 0, tcount = 0;
-  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
-    if (*s_abort) break;
-    const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
-    const long long local = tile - T->tile0;
-    const int tiles_mn = T->tm * T->tn;
-    const int ks = (int)(local / tiles_mn);
-    const int r = (int)(local - (long long)ks * tiles_mn);
-    const int tmi = r / T->tn, tni = r - (r / T->tn) * T->tn;
-    const int kt0 = ks * T->kchunk;
-    const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
-    const int row0 = tmi * 128, col0 = tni * T->ntile;
-    const int ntile = T->ntile;
-    if (threadIdx.x == 0) {
-      // TMA producer
-      const uint32_t bbytes = (uint32_t)ntile * 128u;
-      for (int j = 0; j < nk; ++j) {
-        const uint32_t s = (it + j) % NST, ph = ((it + j) / NST) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, err, 1)) { *s_abort = 1; break; }
-        uint8_t* st = smem + s * SB;
-        mbar_expect_tx(&full[s], (SPLIT ? 2u : 1u) * (A_BYTES + bbytes));
-        tma_load_2d(st, &T->ma, &full[s], (kt0 + j) * KT, row0);
-        tma_load_2d(st + A_BYTES, &T->mb, &full[s], (kt0 + j) * KT, col0);
-        if (SPLIT) {
-          tma_load_2d(st + STAGE_BYTES, &T->ma2, &full[s], (kt0 + j) * KT, row0);
-          tma_load_2d(st + STAGE_BYTES + A_BYTES, &T->mb2, &full[s], (kt0 + j) * KT, col0);
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      uint32_t it = 0;
+      for (long long tile = blockIdx.x; tile < total && !*s_abort; tile += gridDim.x) {
+        const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
+        const long long local = tile - T->tile0;
+        const int tiles_mn = T->tm * T->tn;
+        const int ks = (int)(local / tiles_mn);
+        const int r = (int)(local - (long long)ks * tiles_mn);
+        const int tmi = r / T->tn, tni = r - (r / T->tn) * T->tn;
+        const int kt0 = ks * T->kchunk;
+        const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
+        const int row0 = tmi * 128, col0 = tni * T->ntile;
+        const uint32_t bbytes = (uint32_t)T->ntile * 128u;
+        for (int j = 0; j < nk; ++j, ++it) {
+          const uint32_t s = it % NST, ph = (it / NST) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, err, 1)) { *s_abort = 1; break; }
+          uint8_t* st = smem + s * SB;
+          mbar_expect_tx(&full[s], (SPLIT ? 2u : 1u) * (A_BYTES + bbytes));
+          tma_load_2d(st, &T->ma, &full[s], (kt0 + j) * KT, row0);
+          tma_load_2d(st + A_BYTES, &T->mb, &full[s], (kt0 + j) * KT, col0);
+          if (SPLIT) {
+            tma_load_2d(st + STAGE_BYTES, &T->ma2, &full[s], (kt0 + j) * KT, row0);
+            tma_load_2d(st + STAGE_BYTES + A_BYTES, &T->mb2, &full[s], (kt0 + j) * KT, col0);
+          }
         }
       }
-    } else if (threadIdx.x == 32) {
-      // MMA issuer
-      const uint32_t id = idesc<PREC>(128, ntile);
-      for (int j = 0; j < nk; ++j) {
-        const uint32_t s = (it + j) % NST, ph = ((it + j) / NST) & 1u;
-        if (!mbar_wait(&full[s], ph, err, 2)) { *s_abort = 1; break; }
-        fence_after();
-        uint8_t* st = smem + s * SB;
-        const uint64_t a = sdesc(st);
-        const uint64_t b = sdesc(st + A_BYTES);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) umma<PREC>(tmem, a + 2 * kk, b + 2 * kk, id, (j > 0 || kk > 0) ? 1u : 0u);
-        if (SPLIT) {
-          const uint64_t a2 = sdesc(st + STAGE_BYTES);
-          const uint64_t b2 = sdesc(st + STAGE_BYTES + A_BYTES);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) umma<PREC>(tmem, a + 2 * kk, b2 + 2 * kk, id, 1u);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) umma<PREC>(tmem, a2 + 2 * kk, b + 2 * kk, id, 1u);
-        }
-        umma_commit(&empty[s]);
-      }
-      umma_commit(done);
     }
-    it += nk;
-    // epilogue: thread t owns accumulator row t (tensor-memory lane t)
-    const bool ok = __syncthreads_and(mbar_wait(done, tcount & 1u, err, 3)) != 0;
-    fence_after();
-    if (ok && nk > 0) {
-      const int row = row0 + threadIdx.x;
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      uint32_t it = 0, tcount = 0;
+      for (long long tile = blockIdx.x; tile < total && !*s_abort; tile += gridDim.x, ++tcount) {
+        const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
+        const long long local = tile - T->tile0;
+        const int tiles_mn = T->tm * T->tn;
+        const int ks = (int)(local / tiles_mn);
+        const int kt0 = ks * T->kchunk;
+        const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
+        const uint32_t buf = tcount & 1u;
+        const uint32_t acc = tmem + buf * ACC_COLS;
+        if (!mbar_wait(&acc_empty[buf], ((tcount >> 1) & 1u) ^ 1u, err, 4)) { *s_abort = 1; break; }
+        fence_after();
+        const uint32_t id = idesc<PREC>(128, T->ntile);
+        bool ok = true;
+        for (int j = 0; j < nk; ++j, ++it) {
+          const uint32_t s = it % NST, ph = (it / NST) & 1u;
+          if (!mbar_wait(&full[s], ph, err, 2)) { ok = false; break; }
+          fence_after();
+          uint8_t* st = smem + s * SB;
+          const uint64_t a = sdesc(st);
+          const uint64_t b = sdesc(st + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) umma<PREC>(acc, a + 2 * kk, b + 2 * kk, id, (j > 0 || kk > 0) ? 1u : 0u);
+          if (SPLIT) {
+            const uint64_t a2 = sdesc(st + STAGE_BYTES);
+            const uint64_t b2 = sdesc(st + STAGE_BYTES + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) umma<PREC>(acc, a + 2 * kk, b2 + 2 * kk, id, 1u);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) umma<PREC>(acc, a2 + 2 * kk, b + 2 * kk, id, 1u);
+          }
+          umma_commit(&empty[s]);
+        }
+        umma_commit(&acc_full[buf]);
+        if (!ok) { *s_abort = 1; break; }
+      }
+    }
+  } else {
+    // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31
+    const int quarter = warp & 3;
+    uint32_t tcount = 0;
+    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
+      const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
+      const long long local = tile - T->tile0;
+      const int tiles_mn = T->tm * T->tn;
+      const int ks = (int)(local / tiles_mn);
+      const int r = (int)(local - (long long)ks * tiles_mn);
+      const int tmi = r / T->tn, tni = r - (r / T->tn) * T->tn;
+      const int row0 = tmi * 128, col0 = tni * T->ntile;
+      const int ntile = T->ntile;
+      const uint32_t buf = tcount & 1u;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (tcount >> 1) & 1u, err, 3));
+      if (!ok || *s_abort) { *s_abort = 1; break; }
+      fence_after();
+      const int row = row0 + quarter * 32 + lane;
+      const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
       const bool live = row < T->m;
       long long roff = 0;
       if (live) roff = (long long)(row / T->rpb) * T->bstride + (long long)(row % T->rpb) * T->ldc;
@@ -281,77 +388,16 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const TcTask* __restric
         const int c0 = col0 + cb;
         const int nv = min(32, T->n - c0);
         if (nv <= 0) continue;
-        if (T->mode == 1 || T->mode == 3) {
-          // BF16 rows: a thread owns 32 contiguous outputs = 64 bytes; store
-          // them as four 16-byte vectors when aligned
-          __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
-          if (nv == 32 && ((uintptr_t)C & 15) == 0 && (T->mode == 1 || (T->soff & 7) == 0)) {
-            uint32_t hi[16], lo[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
-              const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
-              const float2 hf = __bfloat1622float2(h);
-              const __nv_bfloat162 l = __floats2bfloat162_rn(f0 - hf.x, f1 - hf.y);
-              hi[j] = *reinterpret_cast<const uint32_t*>(&h);
-              lo[j] = *reinterpret_cast<const uint32_t*>(&l);
-            }
-            uint4* d0 = reinterpret_cast<uint4*>(C);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) d0[q] = make_uint4(hi[4 * q], hi[4 * q + 1], hi[4 * q + 2], hi[4 * q + 3]);
-            if (T->mode == 3) {
-              uint4* d1 = reinterpret_cast<uint4*>(C + T->soff);
-#pragma unroll
-              for (int q = 0; q < 4; ++q) d1[q] = make_uint4(lo[4 * q], lo[4 * q + 1], lo[4 * q + 2], lo[4 * q + 3]);
-            }
-            continue;
-          }
-        }
-        if (T->mode == 2 && nv == 32 && (((uintptr_t)((float*)T->C + roff + c0)) & 15) == 0) {
-          float4* d = reinterpret_cast<float4*>((float*)T->C + roff + c0);
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            d[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
-                               __uint_as_float(v[4 * q + 3]));
-          continue;
-        }
-        if (T->mode == 4) {
-          double* C = (double*)T->C + roff + c0;
-          if (T->beta == 0.0)
-            for (int j = 0; j < nv; ++j) C[j] = T->alpha * (double)__uint_as_float(v[j]);
-          else
-            for (int j = 0; j < nv; ++j) C[j] = T->alpha * (double)__uint_as_float(v[j]) + T->beta * C[j];
-          continue;
-        }
-        if (T->mode == 0) {
-          float* C = (float*)T->C + roff + c0;
-          for (int j = 0; j < nv; ++j) atomicAdd(C + j, __uint_as_float(v[j]));
-        } else if (T->mode == 1) {
-          __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
-          for (int j = 0; j < nv; ++j) C[j] = __float2bfloat16_rn(__uint_as_float(v[j]));
-        } else if (T->mode == 3) {
-          // two-term BF16 split of the FP32 result: [hi | lo]
-          __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
-          for (int j = 0; j < nv; ++j) {
-            const float f = __uint_as_float(v[j]);
-            const __nv_bfloat16 h = __float2bfloat16_rn(f);
-            const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
-            C[j] = h;
-            C[j + T->soff] = l;
-          }
-        } else {
-          float* C = (float*)T->C + roff + c0;
-          for (int j = 0; j < nv; ++j) C[j] = __uint_as_float(v[j]);
-        }
+        store_row(T, roff, c0, nv, v);
       }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
-    if (!ok) *s_abort = 1;
-    fence_before();
-    __syncthreads();
   }
   __syncthreads();
   fence_after();
-  if (warp == 0)
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
@@ -536,7 +582,7 @@ void launch_variant(cudaStream_t st, int grid, const TcTask* d_tasks, int ntasks
                "smem attr");
     attr = true;
   }
-  tc_gemm_kernel<P, S><<<grid, 128, SMEM_BYTES, st>>>(d_tasks, ntasks, total, err);
+  tc_gemm_kernel<P, S><<<grid, TC_THREADS, SMEM_BYTES, st>>>(d_tasks, ntasks, total, err);
 }
 
 void launch_tc_stream(cudaStream_t st, int grid, int prec, const TcTask* d_tasks, int ntasks, long long total,
