@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--M0", type=int, default=None)
     ap.add_argument("--M1", type=int, default=None)
-    ap.add_argument("--dmrg-sweeps", type=int, default=3)
+    ap.add_argument("--dmrg-sweeps", type=int, default=4)
     ap.add_argument("--prec", default="bf16x3", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

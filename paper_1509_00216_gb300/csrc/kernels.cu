@@ -217,6 +217,18 @@ __global__ void take_eigvecs_kernel(const double* __restrict__ V, int n, int m, 
   }
 }
 
+// x[i] += amp * (u_i - 1/2), u_i uniform from the splitmix64 hash of (seed, i)
+__global__ void noise_kernel(long n, double amp, unsigned long long seed, double* __restrict__ x) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    x[i] += amp * (u - 0.5);
+  }
+}
+
 __global__ void f64_to_bf16_kernel(long n, const double* __restrict__ x, __nv_bfloat16* __restrict__ y) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     y[i] = __float2bfloat16_rn((float)x[i]);
@@ -310,6 +322,9 @@ void launch_gather(const GatherTask* d_tasks, int ntasks, int max_elems, cudaStr
 }
 void launch_take_eigvecs(const double* V, int n, int m, int right, double* out, cudaStream_t s) {
   take_eigvecs_kernel<<<elem_grid((long)n * m), 256, 0, s>>>(V, n, m, right, out);
+}
+void launch_noise(long n, double amp, unsigned long long seed, double* x, cudaStream_t s) {
+  noise_kernel<<<elem_grid(n), 256, 0, s>>>(n, amp, seed, x);
 }
 void launch_f64_to_bf16(long n, const double* x, uint16_t* y, cudaStream_t s) {
   f64_to_bf16_kernel<<<elem_grid(n), 256, 0, s>>>(n, x, reinterpret_cast<__nv_bfloat16*>(y));

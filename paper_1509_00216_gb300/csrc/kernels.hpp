@@ -77,6 +77,9 @@ void launch_gather(const GatherTask* d_tasks, int ntasks, int max_elems, cudaStr
 // RIGHT: out[j * n + c] = V[c + (n-1-j) * n]   (rows = kept, cols = basis)
 void launch_take_eigvecs(const double* V, int n, int m, int right, double* out, cudaStream_t s);
 
+// Perturbation x += amp * (uniform - 1/2) from a counter-based hash.
+void launch_noise(long n, double amp, unsigned long long seed, double* x, cudaStream_t s);
+
 // Precision conversion for the tensor-core path.
 void launch_f64_to_bf16(long n, const double* x, uint16_t* y, cudaStream_t s);
 void launch_f64_to_f32(long n, const double* x, float* y, cudaStream_t s);

@@ -658,6 +658,14 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
         double dtol = mixed ? std::max(c.opts.tol, 1e-4) : std::max(c.opts.tol, 1e-13);
         E = davidson(c, P, x.d(), n, dg.d(), dtol, c.opts.max_iter, c.opts.davidson_max_subspace, &conv, dprec);
         all_conv &= conv;
+        if (sw < n_sweeps - 1) {
+          // decaying perturbation of the two-site state before truncation, so
+          // that early sweeps keep states outside the current local optimum
+          // (the last sweep is noise-free)
+          const double amp = 1e-3 * std::pow(0.1, sw) / std::sqrt((double)std::max(n, 1L));
+          launch_noise(n, amp, c.opts.seed * 1000003ull + (unsigned long long)(sw * 2 * k + (right ? 0 : k) + l), x.d(),
+                       c.s());
+        }
         double disc = truncate(c, c.phi0, l, x.d(), M0, right);
         c.max_disc = std::max(c.max_disc, disc);
         invalidate_site(c.f00, l);
