@@ -346,7 +346,7 @@ def gpu_arm(args, rank, world, local_rank):
                         "parallelism": "replicas" if world > 1 else "single",
                         "l2": "working set (environments, fused operators) far above L2"},
                 sweep_s=dev_s / args.steps, sigma_calls=st["sigma_calls"], sigma_kernel_s=kern,
-                stage_s={k: st[k] for k in ("t_plan", "t_rhs", "t_solve", "t_trunc", "t_env")},
+                stage_s={k: st[k] for k in ("t_plan", "t_rhs", "t_solve", "t_trunc", "t_env", "t_fuse_left", "t_fuse_right", "t_tc_prepare")},
                 energies={k: e[k] for k in ("E0", "E2", "E3", "E_lcc2", "E_lcc3", "max_discarded_weight")},
                 roofline=roof, gpu_launches=st["kernel_launches"],
                 e2e={"value": world * flops2 / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,

@@ -57,8 +57,16 @@ typedef enum {
 
 /* FP64 DFMA; TF32 or BF16 tensor-core operands (FP32 accumulation); BF16X3:
    operands split into BF16 hi + lo parts, hi*hi + hi*lo + lo*hi accumulated
-   in FP32 (about 2^-16 relative accuracy) */
-typedef enum { MPSLCC_FP64 = 0, MPSLCC_TF32 = 1, MPSLCC_BF16 = 2, MPSLCC_BF16X3 = 3 } mpslcc_prec;
+   in FP32 (about 2^-17 relative accuracy); BF16X6: three BF16 parts h, m, l,
+   the six products hh hm mh mm hl lh accumulated in FP32 (about 2^-24, the
+   level of the FP32 accumulation; used for residuals) */
+typedef enum {
+  MPSLCC_FP64 = 0,
+  MPSLCC_TF32 = 1,
+  MPSLCC_BF16 = 2,
+  MPSLCC_BF16X3 = 3,
+  MPSLCC_BF16X6 = 4
+} mpslcc_prec;
 
 /* Operators for mpslcc_apply_heff / mpslcc_local_dim. */
 typedef enum {
@@ -129,6 +137,9 @@ typedef struct {
   double t_env;             /*   environment renormalisation                 */
   double t_solve;           /*   local linear solves                         */
   double t_rhs;             /*   right-hand side, projector, diagonal        */
+  double t_fuse_left;       /* wall seconds building L' (all sweeps)         */
+  double t_fuse_right;      /* ... building R'                               */
+  double t_tc_prepare;      /* ... low-precision copies of L', R' and tasks  */
 } mpslcc_stats;
 
 /* Fill *opts with defaults (device 0, FP64, tol 1e-10, max_iter 200, auto

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmpslcc.so")
 
-FP64, TF32, BF16, BF16X3 = 0, 1, 2, 3
+FP64, TF32, BF16, BF16X3, BF16X6 = 0, 1, 2, 3, 4
 OP_H0_11, OP_H0_00, OP_H_10, OP_U_11, OP_S_10, OP_H_11 = range(6)
 MPO_H, MPO_H0, MPO_U, MPO_ID = range(4)
 
@@ -58,7 +58,8 @@ class Stats(C.Structure):
                 ("tc_phase1_bytes", C.c_double), ("tc_phase2_bytes", C.c_double),
                 ("f64_phase1_seconds", C.c_double), ("f64_phase2_seconds", C.c_double),
                 ("tc_launches", C.c_longlong), ("t_plan", C.c_double), ("t_trunc", C.c_double),
-                ("t_env", C.c_double), ("t_solve", C.c_double), ("t_rhs", C.c_double)]
+                ("t_env", C.c_double), ("t_solve", C.c_double), ("t_rhs", C.c_double),
+                ("t_fuse_left", C.c_double), ("t_fuse_right", C.c_double), ("t_tc_prepare", C.c_double)]
 
 
 def _load():

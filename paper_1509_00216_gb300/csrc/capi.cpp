@@ -105,6 +105,7 @@ mpslcc_status mpslcc_create(mpslcc_ctx** out, const mpslcc_opts* opts) {
   if (opts) ctx->c.opts = *opts;
   else mpslcc_default_opts(&ctx->c.opts);
   mpslcc_status st = guard(ctx, [&](Ctx& c) {
+    MPSLCC_REQUIRE(c.opts.prec >= MPSLCC_FP64 && c.opts.prec <= MPSLCC_BF16X6, ST_ARG, "opts.prec out of range");
     c.device = c.opts.device;
     c.host_only = c.device < 0;
     if (c.host_only) return;
@@ -295,7 +296,7 @@ static void apply_heff_dev(Ctx& c, int site, int op, const double* d_psi, double
   need_device(c);
   cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
   MPSLCC_REQUIRE(site >= 0 && site <= c.k - 2, ST_ARG, "site out of range");
-  MPSLCC_REQUIRE(prec >= 0 && prec <= 3, ST_ARG, "bad precision");
+  MPSLCC_REQUIRE(prec >= MPSLCC_FP64 && prec <= MPSLCC_BF16X6, ST_ARG, "bad precision");
   Family& F = family_for(c, op);
   SigmaPlan P;
   make_sigma_plan(c, F, site, P);
@@ -528,6 +529,9 @@ mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out) {
     out->t_plan = c.st.t_plan;
     out->t_trunc = c.st.t_trunc;
     out->t_env = c.st.t_env;
+    out->t_fuse_left = c.st.t_fuse_left;
+    out->t_fuse_right = c.st.t_fuse_right;
+    out->t_tc_prepare = c.st.t_tc_prepare;
     out->t_solve = c.st.t_solve;
     out->t_rhs = c.st.t_rhs;
   });

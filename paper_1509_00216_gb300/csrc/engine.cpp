@@ -18,18 +18,18 @@
 
 namespace mpslcc {
 
-static double now_s() {
+double wall_seconds() {
   timespec ts;
   clock_gettime(CLOCK_MONOTONIC, &ts);
   return ts.tv_sec + 1e-9 * ts.tv_nsec;
 }
 StageTimer::StageTimer(Ctx& c_, double* a) : c(c_), acc(a) {
   cudaStreamSynchronize(c.s());
-  t0 = now_s();
+  t0 = wall_seconds();
 }
 StageTimer::~StageTimer() {
   cudaStreamSynchronize(c.s());
-  *acc += now_s() - t0;
+  *acc += wall_seconds() - t0;
 }
 
 void cuda_check(cudaError_t e, const char* what) {
@@ -679,8 +679,14 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P) {
   P.fam = &F;
   two_site_middle(*F.bra, l, P.mid_b, P.off_b, P.nb);
   two_site_middle(*F.ket, l, P.mid_k, P.off_k, P.nk);
-  make_left_fused(c, F, l, P.mid_b, P.mid_k, P.lf);
-  make_right_fused(c, F, l + 1, P.mid_b, P.mid_k, P.rf);
+  {
+    StageTimer tm(c, &c.st.t_fuse_left);
+    make_left_fused(c, F, l, P.mid_b, P.mid_k, P.lf);
+  }
+  {
+    StageTimer tm(c, &c.st.t_fuse_right);
+    make_right_fused(c, F, l + 1, P.mid_b, P.mid_k, P.rf);
+  }
   const LeftFused& lf = P.lf;
   const RightFused& rf = P.rf;
   P.tt_off.assign(P.mid_b.size(), 0);

@@ -17,6 +17,7 @@ namespace mpslcc {
 
 struct Ctx;
 
+double wall_seconds();  // monotonic host clock
 void cuda_check(cudaError_t e, const char* what);
 
 // Device buffer owned by a context (stream-ordered allocation).
@@ -158,8 +159,10 @@ struct SigmaPlan {
   long long tiles1 = 0, tiles2 = 0;
   bool zero_y = false;
   double flops = 0.0;                  // algorithmic flops of one application
-  // low-precision operand copies and task lists of the tensor-core path
+  // low-precision operand copies and task lists of the tensor-core path:
+  // tc for TF32 / BF16, tc6 for the three-piece layout (BF16X3 and BF16X6)
   struct TcState* tc = nullptr;
+  struct TcState* tc6 = nullptr;
   SigmaPlan() = default;
   SigmaPlan(const SigmaPlan&) = delete;
   SigmaPlan& operator=(const SigmaPlan&) = delete;
@@ -179,6 +182,7 @@ struct Stats {
   double tc_gemm_flops = 0;
   // host wall time per sweep stage (stream-synchronised)
   double t_plan = 0, t_trunc = 0, t_env = 0, t_solve = 0, t_rhs = 0;
+  double t_fuse_left = 0, t_fuse_right = 0, t_tc_prepare = 0;
 };
 
 // Adds the wall time of a scope (after synchronising the stream) to *acc.

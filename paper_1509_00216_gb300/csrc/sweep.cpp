@@ -635,74 +635,143 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
   init_random_mps(c, c.phi0, std::min(M0, 16), true, c.opts.seed);
   double E = 0;
   bool all_conv = true;
+  // one half-sweep of two-site Davidson updates (Eq. EH): products and the
+  // Davidson tolerance in `prec`; `noise` > 0 perturbs each two-site state
+  // before truncation by that amplitude (per unit-norm vector)
+  auto half_sweep = [&](bool right, int prec, double noise, unsigned long long tag) {
+    for (int step = 0; step <= k - 2; ++step) {
+      int l = right ? step : k - 2 - step;
+      SigmaPlan P;
+      make_sigma_plan(c, c.f00, l, P);
+      long n = P.nk;
+      DBuf x, dg;
+      x.alloc(&c, std::max(n, 1L) * sizeof(double));
+      dg.alloc(&c, std::max(n, 1L) * sizeof(double));
+      form_two_site(c, c.phi0, l, x.d());
+      sigma_diag(c, P, dg.d());
+      bool conv = false;
+      // split-BF16 products reach a residual of ~2^-16 |H_eff|: stop there
+      double dtol = prec == MPSLCC_FP64 ? std::max(c.opts.tol, 1e-13) : std::max(c.opts.tol, 1e-4);
+      E = davidson(c, P, x.d(), n, dg.d(), dtol, c.opts.max_iter, c.opts.davidson_max_subspace, &conv, prec);
+      all_conv &= conv;
+      if (noise > 0)
+        launch_noise(n, noise / std::sqrt((double)std::max(n, 1L)), tag * 1000003ull + (unsigned long long)l, x.d(),
+                     c.s());
+      double disc = truncate(c, c.phi0, l, x.d(), M0, right);
+      c.max_disc = std::max(c.max_disc, disc);
+      invalidate_site(c.f00, l);
+      invalidate_site(c.f00, l + 1);
+      if (right) env_update_left(c, c.f00, l, P.lf);
+      else env_update_right(c, c.f00, l + 1, P.rf);
+      if (c.opts.verbose)
+        fprintf(stderr, "[dmrg] %s %s l=%d n=%ld E=%.12f disc=%.2e\n", prec == MPSLCC_FP64 ? "fp64" : "mixed",
+                right ? "R" : "L", l, n, E, disc);
+    }
+  };
+  const int sprec = mixed ? MPSLCC_BF16X3 : MPSLCC_FP64;
   {
-  // mixed precision: every per-site product on the tensor cores (split BF16)
-  GemmPrec gp(c, mixed ? MPSLCC_BF16X3 : MPSLCC_FP64);
-  bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
-  for (int sw = 0; sw < n_sweeps; ++sw) {
-    for (int dir = 0; dir < 2; ++dir) {
-      bool right = dir == 0;
-      for (int step = 0; step <= k - 2; ++step) {
-        int l = right ? step : k - 2 - step;
-        SigmaPlan P;
-        make_sigma_plan(c, c.f00, l, P);
-        long n = P.nk;
-        DBuf x, dg;
-        x.alloc(&c, std::max(n, 1L) * sizeof(double));
-        dg.alloc(&c, std::max(n, 1L) * sizeof(double));
-        form_two_site(c, c.phi0, l, x.d());
-        sigma_diag(c, P, dg.d());
-        bool conv = false;
-        const int dprec = mixed ? MPSLCC_BF16X3 : MPSLCC_FP64;
-        // split-BF16 products reach a residual of ~2^-16 |H_eff|: stop there
-        double dtol = mixed ? std::max(c.opts.tol, 1e-4) : std::max(c.opts.tol, 1e-13);
-        E = davidson(c, P, x.d(), n, dg.d(), dtol, c.opts.max_iter, c.opts.davidson_max_subspace, &conv, dprec);
-        all_conv &= conv;
-        if (sw < n_sweeps - 1) {
-          // decaying perturbation of the two-site state before truncation, so
-          // that early sweeps keep states outside the current local optimum
-          // (the last sweep is noise-free)
-          const double amp = 1e-3 * std::pow(0.1, sw) / std::sqrt((double)std::max(n, 1L));
-          launch_noise(n, amp, c.opts.seed * 1000003ull + (unsigned long long)(sw * 2 * k + (right ? 0 : k) + l), x.d(),
-                       c.s());
-        }
-        double disc = truncate(c, c.phi0, l, x.d(), M0, right);
-        c.max_disc = std::max(c.max_disc, disc);
-        invalidate_site(c.f00, l);
-        invalidate_site(c.f00, l + 1);
-        if (right) env_update_left(c, c.f00, l, P.lf);
-        else env_update_right(c, c.f00, l + 1, P.rf);
-        if (c.opts.verbose)
-          fprintf(stderr, "[dmrg] sweep %d %s l=%d n=%ld E=%.12f disc=%.2e\n", sw, right ? "R" : "L", l, n, E, disc);
-      }
+    // mixed precision: every per-site product on the tensor cores (split BF16)
+    GemmPrec gp(c, sprec);
+    bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
+    for (int sw = 0; sw < n_sweeps; ++sw) {
+      // decaying perturbation so that early sweeps keep states outside the
+      // current local optimum; the last sweep is noise-free
+      const double amp = sw < n_sweeps - 1 ? 1e-3 * std::pow(0.1, sw) : 0.0;
+      for (int dir = 0; dir < 2; ++dir)
+        half_sweep(dir == 0, sprec, amp, c.opts.seed * 7919ull + (unsigned long long)(2 * sw + dir));
     }
   }
-  }
   if (mixed) {
-    // FP64 pass: environments rebuilt in FP64 from the right and a final
-    // FP64 Davidson at position 0; E0 is that eigenvalue
+    // FP64 sweep: the split-BF16 Davidson stops at a residual of ~1e-4, an
+    // eigenvector error that E0 shows only to second order but E2 and E3 to
+    // first; one sweep with FP64 environments and FP64 Davidson (ending at
+    // position 0, whose eigenvalue is E0) brings the bases of every bond to
+    // FP64 accuracy
+    GemmPrec gp(c, MPSLCC_FP64);
     bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
-    SigmaPlan P;
-    make_sigma_plan(c, c.f00, 0, P);
-    long n = P.nk;
-    DBuf x, dg;
-    x.alloc(&c, std::max(n, 1L) * sizeof(double));
-    dg.alloc(&c, std::max(n, 1L) * sizeof(double));
-    form_two_site(c, c.phi0, 0, x.d());
-    sigma_diag(c, P, dg.d());
-    bool conv = false;
-    E = davidson(c, P, x.d(), n, dg.d(), std::max(c.opts.tol, 1e-13), c.opts.max_iter, c.opts.davidson_max_subspace,
-                 &conv, MPSLCC_FP64);
-    all_conv &= conv;
-    truncate(c, c.phi0, 0, x.d(), M0, false);
-    invalidate_site(c.f00, 0);
-    invalidate_site(c.f00, 1);
-    env_update_right(c, c.f00, 1, P.rf);
+    half_sweep(true, MPSLCC_FP64, 0.0, 0);
+    half_sweep(false, MPSLCC_FP64, 0.0, 0);
   }
   c.E0 = E;
   c.have_E0 = true;
   if (!all_conv && c.opts.verbose) fprintf(stderr, "[dmrg] warning: some Davidson solves hit max_iter\n");
   return E;
+}
+
+// One local step of the first-order solve at two-site position l (Eq. 1
+// with n = 1, projector form): b = -Q_loc (P1^T H Phi0 - E0 v) with
+// v = P1^T Phi0 and Q_loc = 1 - v v^T / |v|^2, then Q_loc (H0_eff - E0) Q_loc
+// x = b from the current two-site state of Phi1.  Products in `prec` (the
+// right-hand side in `rprec`); xb receives x.  Returns the local Hylleraas
+// value J = x.Ax - 2 x.b.
+double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, int prec, int rprec, DBuf& xb,
+                 int* its_out, bool* indef_out) {
+  long n = P11.nk, n0 = P10.nk;
+  xb.alloc(&c, std::max(n, 1L) * sizeof(double));
+  DBuf bb, ub, sb, dg, p0;
+  StageTimer* trhs = new StageTimer(c, &c.st.t_rhs);
+  bb.alloc(&c, std::max(n, 1L) * sizeof(double));
+  ub.alloc(&c, std::max(n, 1L) * sizeof(double));
+  sb.alloc(&c, std::max(n, 1L) * sizeof(double));
+  dg.alloc(&c, std::max(n, 1L) * sizeof(double));
+  p0.alloc(&c, std::max(n0, 1L) * sizeof(double));
+  form_two_site(c, c.phi0, l, p0.d());
+  sigma_apply(c, P10, p0.d(), sb.d(), rprec);   // P1^T H Phi0
+  sigma_apply(c, PS, p0.d(), ub.d(), rprec);    // v = P1^T Phi0
+  // b = -(P1^T H Phi0 - E0 v), then project out v
+  copyv(c, bb.d(), ub.d(), n);
+  launch_axpby(n, -1.0, sb.d(), c.E0, bb.d(), c.s());
+  double vn = std::sqrt(std::max(0.0, dev_dot(c, ub.d(), ub.d(), n)));
+  const double* u = nullptr;
+  if (vn > 1e-10) {
+    launch_scale(n, 1.0 / vn, ub.d(), c.s());
+    u = ub.d();
+  }
+  project(c, u, bb.d(), n);
+  form_two_site(c, c.phi1, l, xb.d());
+  sigma_diag(c, P11, dg.d());
+  delete trhs;
+  StageTimer* tsol = new StageTimer(c, &c.st.t_solve);
+  LinOp A{&P11, c.E0, u, Vec()};
+  int its = 0;
+  bool indef = false;
+  double bn = std::sqrt(std::max(0.0, dev_dot(c, bb.d(), bb.d(), n)));
+  if (prec == MPSLCC_FP64) {
+    solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(c.opts.tol, 1e-14), c.opts.max_iter, prec, &its,
+                 &indef);
+  } else {
+    // mixed-precision iterative refinement: residuals r = b - A x with
+    // BF16X6 products (~2^-24) and FP64 vectors, corrections from inner
+    // solves with `prec` products (BF16X3 ~2^-17; TF32 / BF16 coarser)
+    const double inner = prec == MPSLCC_BF16X3 || prec == MPSLCC_BF16X6 ? 1e-4 : 0.05;
+    Vec r, dx, ax;
+    r.alloc(c, n);
+    dx.alloc(c, n);
+    ax.alloc(c, n);
+    project(c, u, xb.d(), n);  // the solution lies in the range of Q_loc
+    for (int ref = 0; ref < std::max(1, c.opts.refine_steps); ++ref) {
+      A.apply(c, xb.d(), ax.d(), MPSLCC_BF16X6);
+      copyv(c, r.d(), bb.d(), n);
+      launch_axpy(n, -1.0, ax.d(), r.d(), c.s());
+      double rn = vnorm(c, r);
+      if (rn <= std::max(c.opts.tol, 1e-14) * bn) break;
+      launch_fill(n, 0.0, dx.d(), c.s());
+      int it2 = 0;
+      solve_linear(c, A, r.d(), dx.d(), dg.d(), n, std::max(inner, c.opts.tol), c.opts.max_iter, prec, &it2, &indef);
+      its += it2;
+      launch_axpy(n, 1.0, dx.d(), xb.d(), c.s());
+    }
+  }
+  // local Hylleraas value J = x.Ax - 2 x.b with residual-precision products
+  // (the FP64 value of the final state comes from mpslcc_energy)
+  Vec ax;
+  ax.alloc(c, n);
+  A.apply(c, xb.d(), ax.d(), rprec);
+  double J = dev_dot(c, xb.d(), ax.d(), n) - 2.0 * dev_dot(c, xb.d(), bb.d(), n);
+  delete tsol;
+  *its_out = its;
+  *indef_out = indef;
+  return J;
 }
 
 double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
@@ -721,7 +790,8 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
   int prec = c.opts.prec;
   const bool mixed = prec != MPSLCC_FP64;
   GemmPrec gp(c, mixed ? MPSLCC_BF16X3 : MPSLCC_FP64);
-  const int rprec = mixed ? MPSLCC_BF16X3 : MPSLCC_FP64;
+  // right-hand side and residuals: BF16X6 products in mixed precision
+  const int rprec = mixed ? MPSLCC_BF16X6 : MPSLCC_FP64;
   double J = 0, E2 = 0;
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
@@ -742,69 +812,11 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
           make_sigma_plan(c, c.s10, l, PS);
           if (prec != MPSLCC_FP64) tc_prepare(c, P11, MPSLCC_BF16X3);
         }
-        StageTimer* trhs = new StageTimer(c, &c.st.t_rhs);
-        long n = P11.nk, n0 = P10.nk;
-        DBuf xb, bb, ub, vb, sb, dg, p0;
-        xb.alloc(&c, std::max(n, 1L) * sizeof(double));
-        bb.alloc(&c, std::max(n, 1L) * sizeof(double));
-        ub.alloc(&c, std::max(n, 1L) * sizeof(double));
-        sb.alloc(&c, std::max(n, 1L) * sizeof(double));
-        dg.alloc(&c, std::max(n, 1L) * sizeof(double));
-        p0.alloc(&c, std::max(n0, 1L) * sizeof(double));
-        form_two_site(c, c.phi0, l, p0.d());
-        sigma_apply(c, P10, p0.d(), sb.d(), rprec);   // P1^T H Phi0
-        sigma_apply(c, PS, p0.d(), ub.d(), rprec);    // v = P1^T Phi0
-        // b = -(P1^T H Phi0 - E0 v), then project out v
-        copyv(c, bb.d(), ub.d(), n);
-        launch_axpby(n, -1.0, sb.d(), c.E0, bb.d(), c.s());
-        double vn = std::sqrt(std::max(0.0, dev_dot(c, ub.d(), ub.d(), n)));
-        const double* u = nullptr;
-        if (vn > 1e-10) {
-          launch_scale(n, 1.0 / vn, ub.d(), c.s());
-          u = ub.d();
-        }
-        project(c, u, bb.d(), n);
-        form_two_site(c, c.phi1, l, xb.d());
-        sigma_diag(c, P11, dg.d());
-        delete trhs;
-        StageTimer* tsol = new StageTimer(c, &c.st.t_solve);
-        LinOp A{&P11, c.E0, u, Vec()};
+        DBuf xb;
         int its = 0;
         bool indef = false;
-        double bn = std::sqrt(std::max(0.0, dev_dot(c, bb.d(), bb.d(), n)));
-        if (prec == MPSLCC_FP64 || prec == MPSLCC_BF16X3) {
-          // one precision throughout (BF16X3: split-BF16 products, ~2^-16)
-          solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(c.opts.tol, 1e-14), c.opts.max_iter, prec, &its,
-                       &indef);
-        } else {
-          // iterative refinement: inner solves with plain TF32 / BF16 sigma
-          // products, residuals r = b - A x with split-BF16 products and
-          // FP64 vectors
-          Vec r, dx, ax;
-          r.alloc(c, n);
-          dx.alloc(c, n);
-          ax.alloc(c, n);
-          for (int ref = 0; ref < std::max(1, c.opts.refine_steps); ++ref) {
-            A.apply(c, xb.d(), ax.d(), MPSLCC_BF16X3);
-            copyv(c, r.d(), bb.d(), n);
-            launch_axpy(n, -1.0, ax.d(), r.d(), c.s());
-            double rn = vnorm(c, r);
-            if (rn <= std::max(c.opts.tol, 1e-14) * bn) break;
-            launch_fill(n, 0.0, dx.d(), c.s());
-            int it2 = 0;
-            solve_linear(c, A, r.d(), dx.d(), dg.d(), n, 0.05, c.opts.max_iter, prec, &it2, &indef);
-            its += it2;
-            launch_axpy(n, 1.0, dx.d(), xb.d(), c.s());
-          }
-        }
-        // local Hylleraas value J = x.Ax - 2 x.b in the sweep's precision (the
-        // FP64 value of the final state comes from mpslcc_energy)
-        Vec ax;
-        ax.alloc(c, n);
-        A.apply(c, xb.d(), ax.d(), rprec);
-        J = dev_dot(c, xb.d(), ax.d(), n) - 2.0 * dev_dot(c, xb.d(), bb.d(), n);
+        J = lcc_local(c, P11, P10, PS, l, prec, rprec, xb, &its, &indef);
         E2 = J;
-        delete tsol;
         double disc;
         {
           StageTimer tm(c, &c.st.t_trunc);
@@ -826,7 +838,7 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
           env_update_right(c, c.s10, l + 1, PS.rf);
         }
         if (c.opts.verbose)
-          fprintf(stderr, "[lcc] sweep %d %s l=%d n=%ld its=%d%s J=%.12f disc=%.2e\n", sw, right ? "R" : "L", l, n,
+          fprintf(stderr, "[lcc] sweep %d %s l=%d n=%ld its=%d%s J=%.12f disc=%.2e\n", sw, right ? "R" : "L", l, P11.nk,
                   its, indef ? " (minres)" : "", J, disc);
       }
     }
@@ -871,7 +883,7 @@ double expect_fp64(Ctx& c, MPS* bra, int mpo, MPS* ket) {
 // with s = <Phi1|Phi0>, Q Phi1 = Phi1 - s Phi0 and b = -Q H Phi0,
 //   J = <QPhi1|(H0 - E0)|QPhi1> - 2<QPhi1|b>
 //     = <1|H0|1> - E0 <1|1> - 2 s (<1|H0|0> - E0 s) + 2 (<1|H|0> - s E0),
-// and E3 = <Phi1|U|Phi1>.
+// and E3 = <QPhi1|U|QPhi1> = <1|U|1> - 2 s (<1|H|0> - <1|H0|0>).
 void compute_energies(Ctx& c) {
   MPSLCC_REQUIRE(c.phi1.present && c.phi0.present, ST_STATE, "energies need Phi0 and Phi1");
   double A = expect_fp64(c, &c.phi1, MPO_H0, &c.phi1);
@@ -883,7 +895,9 @@ void compute_energies(Ctx& c) {
   c.E2 = c.J;
   c.ovl01 = s;
   c.norm1 = N1;
-  c.E3 = expect_fp64(c, &c.phi1, MPO_U, &c.phi1);
+  // E3 of the projected state Q Phi1 = Phi1 - s Phi0: <0|U|0> = 0 (U has no
+  // block inside the reference class) and <0|U|1> = g - h
+  c.E3 = expect_fp64(c, &c.phi1, MPO_U, &c.phi1) - 2.0 * s * (g - h);
   c.e3_valid = true;
   c.e_valid = true;
 }

@@ -38,7 +38,8 @@ struct alignas(64) TcTask {
   int ntile;            // UMMA N (multiple of 16, <= 256)
   int tm, tn;
   int mode;             // 0: FP32 atomic add, 1: BF16 store, 2: FP32 store,
-                        // 3: split BF16 store (hi at +0, lo at +soff), 4: FP64 alpha/beta store
+                        // 3: split BF16 store (hi at +0, lo at +soff), 4: FP64 alpha/beta store,
+                        // 5: three-piece BF16 store, six B-side blocks at +j soff
   int split;            // operands are hi + lo pairs: acc += Ah Bh + Ah Bl + Al Bh
   long long soff;
   double alpha, beta;   // mode 4: FP64 store C = alpha acc + beta C
@@ -209,6 +210,50 @@ __device__ __forceinline__ void store_row(const TcTask* T, long long roff, int c
       }
       return;
     }
+  }
+  if (T->mode == 5) {
+    // three-piece BF16 split of the FP32 result (exact: 3 x 8 bits), written
+    // as the six B-side blocks [h m m h l h] at +j soff
+    __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
+    if (nv == 32 && ((uintptr_t)C & 15) == 0 && (T->soff & 7) == 0) {
+      uint32_t ph[16], pm[16], pl[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+        const float2 hf = __bfloat1622float2(h);
+        const float r0 = f0 - hf.x, r1 = f1 - hf.y;
+        const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+        const float2 mf = __bfloat1622float2(m);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+        ph[j] = *reinterpret_cast<const uint32_t*>(&h);
+        pm[j] = *reinterpret_cast<const uint32_t*>(&m);
+        pl[j] = *reinterpret_cast<const uint32_t*>(&l);
+      }
+      const uint32_t* blk[6] = {ph, pm, pm, ph, pl, ph};
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        uint4* d = reinterpret_cast<uint4*>(C + b * T->soff);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          d[q] = make_uint4(blk[b][4 * q], blk[b][4 * q + 1], blk[b][4 * q + 2], blk[b][4 * q + 3]);
+      }
+      return;
+    }
+    for (int j = 0; j < nv; ++j) {
+      const float f = __uint_as_float(v[j]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(f);
+      const float r = f - __bfloat162float(h);
+      const __nv_bfloat16 m = __float2bfloat16_rn(r);
+      const __nv_bfloat16 l = __float2bfloat16_rn(r - __bfloat162float(m));
+      C[j] = h;
+      C[j + T->soff] = m;
+      C[j + 2 * T->soff] = m;
+      C[j + 3 * T->soff] = h;
+      C[j + 4 * T->soff] = l;
+      C[j + 5 * T->soff] = h;
+    }
+    return;
   }
   if (T->mode == 2 && nv == 32 && (((uintptr_t)((float*)T->C + roff + c0)) & 15) == 0) {
     float4* d = reinterpret_cast<float4*>((float*)T->C + roff + c0);
@@ -409,7 +454,10 @@ struct ConvTask {
   long long s_src, s_dst;
   int pattern;          // 0 plain; 1 split BF16: hi at +0, lo at +soff;
                         // 2 / 3: three-piece split h, m, l written as six blocks at
-                        // +j soff, [h h m h m l] (A side) / [h m h l m h] (B side)
+                        // +j soff, [h h m m h l] (A side) / [h m m h l h] (B side):
+                        // block by block the products are hh hm mm mh hl lh, and
+                        // blocks 0 and 2 alone hold the hi / lo pair of the
+                        // two-piece split on both sides
   long long soff;
   int trans;            // read the source transposed: dst(r, c) = src[c * src_ld + r]
   long long tile0;
@@ -461,7 +509,7 @@ __global__ void conv_kernel(const ConvTask* __restrict__ t, int ntasks, long lon
         const double r1 = v - (double)__bfloat162float(h);
         const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
         const __nv_bfloat16 l = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(m)));
-        const __nv_bfloat16 pa[6] = {h, h, m, h, m, l}, pb[6] = {h, m, h, l, m, h};
+        const __nv_bfloat16 pa[6] = {h, h, m, m, h, l}, pb[6] = {h, m, m, h, l, h};
         const __nv_bfloat16* pp = T.pattern == 2 ? pa : pb;
 #pragma unroll
         for (int j = 0; j < 6; ++j) d[j * T.soff] = pp[j];
@@ -553,13 +601,14 @@ TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long 
   t.tm = (m + 127) / 128;
   t.tn = (n + t.ntile - 1) / t.ntile;
   // output range check
-  const int es = (mode == 1 || mode == 3) ? 2 : (mode == 4 ? 8 : 4);
+  const int es = (mode == 1 || mode == 3 || mode == 5) ? 2 : (mode == 4 ? 8 : 4);
   long long last = (long long)((m - 1) / rpb) * bstride + (long long)((m - 1) % rpb) * ldc + (n - 1);
   for (int r = 0; r < std::min(m, rpb); ++r) {
     long long l2 = (long long)((m - 1 - r) / rpb) * bstride + (long long)((m - 1 - r) % rpb) * ldc + (n - 1);
     last = std::max(last, l2);
   }
   if (mode == 3) last += soff;
+  if (mode == 5) last += 5 * soff;
   t.soff = soff;
   c.check_bytes(C, (last + 1) * es, "tc output");
   return t;
@@ -645,35 +694,49 @@ void check_err(Ctx& c, DBuf& err) {
 
 // Low-precision state of one sigma plan.
 struct TcState {
-  int prec = -1;
-  DBuf lcat, rstk, tt, x, y, t1, t2, conv, convx, err;
+  int layout = -1;      // operand precision class: TF32, BF16 or BF16X3 (the
+                        // three-piece six-block layout, serving BF16X3 and BF16X6)
+  DBuf lcat, rstk, tt, x, y, conv, convx, err;
   std::vector<long> lcat_off, K8, tt_off, x_off;
   std::vector<long> stk_off;
   std::vector<ConvTask> xconv;
-  int n1 = 0, n2 = 0;
-  long long tiles1 = 0, tiles2 = 0;
-  double bytes1 = 0, bytes2 = 0;
+  // task lists per sigma variant: [0] the layout's own precision (TF32, BF16
+  // or BF16X3), [1] BF16X6 (six-block layout only)
+  DBuf t1[2], t2[2];
+  int n1[2] = {0, 0}, n2[2] = {0, 0};
+  long long tiles1[2] = {0, 0}, tiles2[2] = {0, 0};
+  double bytes1[2] = {0, 0}, bytes2[2] = {0, 0};
 };
 
 void tc_release(SigmaPlan& P) {
-  if (P.tc) {
-    delete P.tc;
-    P.tc = nullptr;
-  }
+  delete P.tc;
+  delete P.tc6;
+  P.tc = nullptr;
+  P.tc6 = nullptr;
 }
 
 SigmaPlan::~SigmaPlan() { tc_release(*this); }
 
+// Low-precision copies of the fused operators of one sigma plan and the task
+// lists of both sigma phases.  BF16X3 and BF16X6 share one copy: every
+// operand row holds six blocks of the three-piece split (h, m, l), A side
+// [h h m m h l] and B side [h m m h l h].  The full rows give the six products
+// of BF16X6 (error about 2^-24 relative, at the level of the FP32
+// accumulation); blocks 0 and 2 alone are the hi / lo pair of BF16X3
+// (hi*hi + hi*lo + lo*hi, about 2^-17).
 void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
-  if (P.tc && P.tc->prec == prec) return;
-  tc_release(P);
+  const int layout = (prec == MPSLCC_BF16X3 || prec == MPSLCC_BF16X6) ? MPSLCC_BF16X3 : prec;
+  TcState*& slot = layout == MPSLCC_BF16X3 ? P.tc6 : P.tc;
+  if (slot && slot->layout == layout) return;
+  StageTimer tm(c, &c.st.t_tc_prepare);
+  delete slot;
+  slot = nullptr;
   TcState* S = new TcState();
-  P.tc = S;
-  S->prec = prec;
-  const int es = esize(prec);
-  // split mode: every operand row stores its BF16 hi part, then its lo part
-  // (K blocks [hi | lo]); the kernel accumulates hi*hi + hi*lo + lo*hi
-  const int sp = prec == MPSLCC_BF16X3 ? 2 : 1;
+  slot = S;
+  S->layout = layout;
+  const int es = esize(layout);
+  const bool six = layout == MPSLCC_BF16X3;
+  const int sp = six ? 6 : 1;
   const LeftFused& lf = P.lf;
   const RightFused& rf = P.rf;
   const size_t nbk = P.mid_b.size(), nkk = P.mid_k.size();
@@ -718,7 +781,8 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   zalloc(S->x, xsz, es);
   zalloc(S->y, std::max(P.nb, 1L), 4);
   zalloc(S->err, 4, 1);
-  // FP64 -> low precision copies of L' and R'
+  // FP64 -> low precision copies of L' (A side of phase 2) and R' (A side of
+  // phase 1)
   std::vector<ConvTask> cv;
   for (size_t bi = 0; bi < nbk; ++bi) {
     int rows = lf.FLb.d[lf.kb[bi]];
@@ -735,7 +799,7 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
       t.batch = sg.nw;
       t.s_src = sg.width;
       t.s_dst = pad8(sg.width);
-      t.pattern = sp == 2 ? 1 : 0;
+      t.pattern = six ? 2 : 0;
       t.soff = S->K8[bi];
       cv.push_back(t);
     }
@@ -752,12 +816,12 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     t.src_ld = rk;
     t.dst_ld = (int)(sp * pad8(rk));
     t.batch = 1;
-    t.pattern = sp == 2 ? 1 : 0;
+    t.pattern = six ? 2 : 0;
     t.soff = pad8(rk);
     cv.push_back(t);
   }
-  run_conv(c, prec, cv, S->conv);
-  // per-call conversion of the input vector
+  run_conv(c, layout, cv, S->conv);
+  // per-call conversion of the input vector (B side of phase 1)
   S->xconv.clear();
   for (size_t ki = 0; ki < nkk; ++ki) {
     ConvTask t;
@@ -769,72 +833,84 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     t.src_ld = t.cols;
     t.dst_ld = (int)(sp * pad8(t.cols));
     t.batch = 1;
-    t.pattern = sp == 2 ? 1 : 0;
+    t.pattern = six ? 3 : 0;
     t.soff = pad8(t.cols);
     S->xconv.push_back(t);
   }
-  // phase 1: T_w^T = R'_w psi^T for all channels of a class in one tall GEMM
-  const int mode1 = sp == 2 ? 3 : (prec == MPSLCC_TF32 ? 2 : 1);
-  std::vector<TcTask> t1, t2;
-  for (size_t si = 0; si < rf.stk.size(); ++si) {
-    const auto& st = rf.stk[si];
-    int bi = st.bidx, ki = st.kidx;
-    const LeftFused::Seg* sg = lf.find_seg(bi, st.cls);
-    size_t g = sg - lf.seg[bi].data();
-    int rb = rf.FRb.d[rf.kb[bi]], rk = rf.FRk.d[rf.kk[ki]], lk = lf.FLk.d[lf.kk[ki]];
-    long kk = sp * pad8(rk);
-    void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + koff8[bi][g]) * es;
-    t1.push_back(make_task(c, prec, (char*)S->rstk.p + (size_t)S->stk_off[si] * es, kk,
-                           (char*)S->x.p + (size_t)S->x_off[ki] * es, kk, st.nw * rb, lk,
-                           (int)(sp == 2 ? rk : kk), C, (int)(sp * S->K8[bi]), rb, pad8(lk), mode1, 1, S->K8[bi],
-                           pad8(rk)));
-    // algorithmic bytes: operands and result once (hi + lo parts in split mode)
-    S->bytes1 += (double)es * sp * ((double)st.nw * rb * rk + (double)lk * rk + (double)st.nw * rb * lk);
-  }
-  // phase 2: sigma = Lcat Tt^T, split over K
   long long base = 0;
   for (size_t bi = 0; bi < nbk; ++bi) {
     int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
     base += (long long)((lb + 127) / 128) * ((rb + 255) / 256);
   }
   const long long target = 2LL * sm_count(c);
-  for (size_t bi = 0; bi < nbk; ++bi) {
-    if (S->K8[bi] == 0) continue;
-    int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
-    long KK = sp * S->K8[bi];
-    int ks = (int)std::max(1LL, (target + base - 1) / std::max(1LL, base));
-    t2.push_back(make_task(c, prec, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, KK,
-                           (char*)S->tt.p + (size_t)S->tt_off[bi] * es, KK, lb, rb, (int)S->K8[bi],
-                           (float*)S->y.p + P.off_b[bi], rb, 1 << 30, 0, 0, ks, 0, S->K8[bi]));
-    S->bytes2 += (double)es * sp * ((double)lb * S->K8[bi] + (double)rb * S->K8[bi]) + 4.0 * lb * rb;
+  for (int v = 0; v < (six ? 2 : 1); ++v) {
+    // v = 0: the layout's own precision; v = 1: BF16X6 (plain BF16 kernel over
+    // all six blocks)
+    const int kp = v == 1 ? MPSLCC_BF16 : layout;
+    const int pcs = v == 1 ? 6 : (six ? 2 : 1);  // pieces read per element
+    std::vector<TcTask> t1, t2;
+    // phase 1: T_w^T = R'_w psi^T for all channels of a class in one tall GEMM
+    const int mode1 = v == 1 ? 5 : (six ? 3 : (layout == MPSLCC_TF32 ? 2 : 1));
+    for (size_t si = 0; si < rf.stk.size(); ++si) {
+      const auto& st = rf.stk[si];
+      int bi = st.bidx, ki = st.kidx;
+      const LeftFused::Seg* sg = lf.find_seg(bi, st.cls);
+      size_t g = sg - lf.seg[bi].data();
+      int rb = rf.FRb.d[rf.kb[bi]], rk = rf.FRk.d[rf.kk[ki]], lk = lf.FLk.d[lf.kk[ki]];
+      const long pitch = sp * pad8(rk);
+      const int kk = v == 1 ? (int)pitch : rk;
+      void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + koff8[bi][g]) * es;
+      // split tasks: lo parts in block 2 of both operands (and of the output)
+      const long long so = v == 1 ? S->K8[bi] : 2 * S->K8[bi];
+      t1.push_back(make_task(c, kp, (char*)S->rstk.p + (size_t)S->stk_off[si] * es, pitch,
+                             (char*)S->x.p + (size_t)S->x_off[ki] * es, pitch, st.nw * rb, lk, kk, C,
+                             (int)(sp * S->K8[bi]), rb, pad8(lk), mode1, 1, six ? so : 0, six ? 2 * pad8(rk) : 0));
+      // algorithmic bytes: operands and result once, per piece read or written
+      S->bytes1[v] += (double)es * pcs * ((double)st.nw * rb * rk + (double)lk * rk + (double)st.nw * rb * lk);
+    }
+    // phase 2: sigma = Lcat Tt^T, split over K
+    for (size_t bi = 0; bi < nbk; ++bi) {
+      if (S->K8[bi] == 0) continue;
+      int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+      const long pitch = sp * S->K8[bi];
+      const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
+      int ks = (int)std::max(1LL, (target + base - 1) / std::max(1LL, base));
+      t2.push_back(make_task(c, kp, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, pitch,
+                             (char*)S->tt.p + (size_t)S->tt_off[bi] * es, pitch, lb, rb, kk,
+                             (float*)S->y.p + P.off_b[bi], rb, 1 << 30, 0, 0, ks, 0,
+                             (six && v == 0) ? 2 * S->K8[bi] : 0));
+      S->bytes2[v] += (double)es * pcs * ((double)lb * S->K8[bi] + (double)rb * S->K8[bi]) + 4.0 * lb * rb;
+    }
+    S->n1[v] = (int)t1.size();
+    S->n2[v] = (int)t2.size();
+    S->tiles1[v] = plan_tc(t1);
+    S->tiles2[v] = plan_tc(t2);
+    S->t1[v].alloc(&c, std::max<size_t>(t1.size(), 1) * sizeof(TcTask));
+    S->t2[v].alloc(&c, std::max<size_t>(t2.size(), 1) * sizeof(TcTask));
+    if (!t1.empty())
+      cuda_check(cudaMemcpyAsync(S->t1[v].p, t1.data(), t1.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
+                 "tc tasks");
+    if (!t2.empty())
+      cuda_check(cudaMemcpyAsync(S->t2[v].p, t2.data(), t2.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
+                 "tc tasks");
   }
-  S->n1 = (int)t1.size();
-  S->n2 = (int)t2.size();
-  S->tiles1 = plan_tc(t1);
-  S->tiles2 = plan_tc(t2);
-  S->t1.alloc(&c, std::max<size_t>(t1.size(), 1) * sizeof(TcTask));
-  S->t2.alloc(&c, std::max<size_t>(t2.size(), 1) * sizeof(TcTask));
-  if (!t1.empty())
-    cuda_check(cudaMemcpyAsync(S->t1.p, t1.data(), t1.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
-               "tc tasks");
-  if (!t2.empty())
-    cuda_check(cudaMemcpyAsync(S->t2.p, t2.data(), t2.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
-               "tc tasks");
   cuda_check(cudaStreamSynchronize(c.s()), "tc prepare sync");
 }
 
 void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
   tc_prepare(c, P, prec);
-  TcState* S = P.tc;
+  TcState* S = (prec == MPSLCC_BF16X3 || prec == MPSLCC_BF16X6) ? P.tc6 : P.tc;
+  const int v = prec == MPSLCC_BF16X6 ? 1 : 0;
+  const int kp = v == 1 ? MPSLCC_BF16 : S->layout;
   if (P.nk > 0)
     cuda_check(cudaMemcpyAsync(P.xin.p, x, P.nk * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma in");
   std::vector<ConvTask> xc = S->xconv;
-  run_conv(c, S->prec, xc, S->convx);
+  run_conv(c, S->layout, xc, S->convx);
   cuda_check(cudaMemsetAsync(S->y.p, 0, std::max(P.nb, 1L) * 4, c.s()), "sigma zero");
   cudaEventRecord(c.ev_p0, c.s());
-  launch_tc(c, S->prec, (const TcTask*)S->t1.p, S->n1, S->tiles1, (int*)S->err.p);
+  launch_tc(c, kp, (const TcTask*)S->t1[v].p, S->n1[v], S->tiles1[v], (int*)S->err.p);
   cudaEventRecord(c.ev_p1, c.s());
-  launch_tc(c, S->prec, (const TcTask*)S->t2.p, S->n2, S->tiles2, (int*)S->err.p);
+  launch_tc(c, kp, (const TcTask*)S->t2[v].p, S->n2[v], S->tiles2[v], (int*)S->err.p);
   cudaEventRecord(c.ev_p2, c.s());
   launch_f32_to_f64(P.nb, (const float*)S->y.p, y, c.s());
   c.st.kernel_launches++;
@@ -844,8 +920,8 @@ void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
   cudaEventElapsedTime(&m2, c.ev_p1, c.ev_p2);
   c.st.tc_phase1_s += m1 * 1e-3;
   c.st.tc_phase2_s += m2 * 1e-3;
-  c.st.tc_phase1_bytes += S->bytes1;
-  c.st.tc_phase2_bytes += S->bytes2;
+  c.st.tc_phase1_bytes += S->bytes1[v];
+  c.st.tc_phase2_bytes += S->bytes2[v];
   c.st.tc_launches += 2;
   c.st.sigma_calls++;
   c.st.sigma_flops += P.flops;
@@ -1040,6 +1116,7 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
 // ---------------------------------------------------------------------------
 void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
   if (tasks.empty()) return;
+  const double th0 = c.opts.verbose >= 2 ? wall_seconds() : 0.0;
   struct Key {
     const double* p;
     int rows, cols, ld, trans;
@@ -1113,9 +1190,18 @@ void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
              "tc gemm tasks");
   c.tc_err.ensure(&c, 16);
   cuda_check(cudaMemsetAsync(c.tc_err.p, 0, 16, c.s()), "tc err zero");
+  const double th1 = c.opts.verbose >= 2 ? wall_seconds() : 0.0;
   launch_tc(c, MPSLCC_BF16, (const TcTask*)c.tc_gemm_tasks.p, (int)tt.size(), tiles, (int*)c.tc_err.p);
-  for (const auto& j : jobs) c.st.tc_gemm_flops += 2.0 * j.m * j.n * j.k;
+  double fl = 0;
+  for (const auto& j : jobs) fl += 2.0 * j.m * j.n * j.k;
+  c.st.tc_gemm_flops += fl;
   check_err(c, c.tc_err);
+  if (c.opts.verbose >= 2) {
+    long conv_elems = 0;
+    for (const auto& t : cv) conv_elems += (long)t.rows * t.cols;
+    fprintf(stderr, "[fp64-tc] tasks=%zu jobs=%zu conv=%zu conv_elems=%ld flops=%.3e host_s=%.4f total_s=%.4f\n",
+            tasks.size(), jobs.size(), cv.size(), conv_elems, fl, th1 - th0, wall_seconds() - th0);
+  }
 }
 
 }  // namespace mpslcc

@@ -127,3 +127,19 @@ def test_full_active_space_gives_fci(mpslcc):
         e = ctx.energy()
     assert abs(E0 - Efci) <= 1e-10
     assert abs(e["E2"]) <= 1e-10 and abs(e["E3"]) <= 1e-10
+
+
+@pytest.mark.parametrize("prec,tol", [("BF16X3", 1e-4), ("BF16X6", 4e-6)])
+def test_sigma_low_precision_all_operators(mpslcc, small_case, prec, tol):
+    """The split-BF16 tensor-core sigma of every operator family (including the
+    transition and overlap ones, whose bra and ket differ) stays within the
+    split's accuracy of the FP64 sigma."""
+    ctx = small_case["ctx"]
+    for l in range(5):
+        for op in (mpslcc.OP_H0_11, mpslcc.OP_U_11, mpslcc.OP_H_11, mpslcc.OP_H0_00, mpslcc.OP_H_10,
+                   mpslcc.OP_S_10):
+            n_out, n_in = ctx.local_dim(l, op)
+            psi = synth.random_vector(n_in, seed=300 + 10 * l + op)
+            s64 = ctx.apply_heff(l, op, psi)
+            slp = ctx.apply_heff(l, op, psi, prec=getattr(mpslcc, prec))
+            assert _rel(slp, s64) <= tol, (op, l, _rel(slp, s64))

@@ -81,8 +81,10 @@ def case6(mpslcc):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec,tol", [("BF16", 3e-2), ("TF32", 4e-3), ("BF16X3", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("BF16", 3e-2), ("TF32", 4e-3), ("BF16X3", 1e-4), ("BF16X6", 1e-6)])
 def test_sigma_low_precision_close_to_fp64(mpslcc, case6, prec, tol):
+    """BF16X6 (three BF16 parts, six products) is limited by the FP32
+    accumulation, about 2^-24 per rounding."""
     for l in range(5):
         n, _ = case6.local_dim(l, mpslcc.OP_H0_11)
         psi = synth.random_vector(n, 9 + l)
@@ -94,11 +96,11 @@ def test_sigma_low_precision_close_to_fp64(mpslcc, case6, prec, tol):
 
 @pytest.mark.parametrize("prec,tol", [("BF16X3", 1e-6)])
 def test_mixed_precision_lcc_matches_fp64(mpslcc, prec, tol):
-    """Mixed-precision sweeps (split-BF16 tensor-core products, FP64 vectors)
-    followed by FP64 evaluation passes reach the oracle's E0 and E2 to 1e-6 at
-    exact bond dimension (L=8 chain).  E3 = <Phi1|U|Phi1> is first order in
-    the wavefunction error (E2, a Hylleraas minimum, is second order), so it
-    carries the ~2^-16 operator error of the local solves: bound 5e-6."""
+    """Mixed-precision sweeps reach the oracle's E0, E2 and E3 to 1e-6 at exact
+    bond dimension (L=8 chain).  The reference ends with an FP64 sweep; the
+    local LCC solves refine split-BF16 (BF16X3) corrections against BF16X6
+    residuals, so the first-order state is accurate to ~2^-24 relative, which
+    E3 = <Phi1|U|Phi1> (first order in the state's error) needs."""
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_energies.json")))
     g = g["hubbard1d_L8_U4"]
     c = synth.config(0)
@@ -110,4 +112,4 @@ def test_mixed_precision_lcc_matches_fp64(mpslcc, prec, tol):
         e = ctx.energy()
     assert abs(e["E0"] - g["E0"]) < 1e-8
     assert abs(e["E2"] - g["E2"]) < tol, (e["E2"], g["E2"])
-    assert abs(e["E3"] - g["E3"]) < 5 * tol
+    assert abs(e["E3"] - g["E3"]) < tol, (e["E3"], g["E3"])
