@@ -323,6 +323,14 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
   Fused FL = fuse_left(m.bond[l], m.mask[l]);
   Fused FR = fuse_right(m.mask[l + 1], m.bond[l + 2]);
   int ns = (int)mid.size();
+  const bool prof = c.opts.verbose >= 2;
+  double tp[5] = {0, 0, 0, 0, 0};
+  auto mark = [&](int i) {
+    if (!prof) return;
+    cudaStreamSynchronize(c.s());
+    tp[i] = wall_seconds();
+  };
+  mark(0);
   std::vector<int> dl(ns), dr(ns), nd(ns);
   std::vector<long> roff(ns), woff(ns);
   long rtot = 0, wtot = 0;
@@ -362,6 +370,7 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     gt.push_back(t);
   }
   run_gemm_tasks(c, gt);
+  mark(1);
   // FP64 eigendecompositions (cuSOLVER), eigenvalues ascending.  The
   // sectors are independent: they run concurrently on NEIG side streams,
   // largest first, each stream with its own handle and workspace.
@@ -407,6 +416,7 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
   std::vector<double> hw(std::max(wtot, 1L));
   cuda_check(cudaMemcpyAsync(hw.data(), w.p, wtot * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "eig d2h");
   cuda_check(cudaStreamSynchronize(c.s()), "eig sync");
+  mark(2);
   // keep the M largest weights; ties by (sector, index)
   struct Ent { double v; int s, j; };
   std::vector<Ent> all;
@@ -446,6 +456,7 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     isz += (long)nd[i] * keep[i];
     csz += (long)(moving_right ? dr[i] : dl[i]) * keep[i];
   }
+  mark(3);
   DBuf iso, cen;
   iso.alloc(&c, std::max(isz, 1L) * sizeof(double));
   cen.alloc(&c, std::max(csz, 1L) * sizeof(double));
@@ -486,6 +497,10 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     set_site_rf(c, m, l + 1, std::move(iso));
     set_site_lf(c, m, l, std::move(cen));
   }
+  mark(4);
+  if (prof)
+    fprintf(stderr, "[trunc] l=%d sectors=%d nmax=%d rho_s=%.4f eigh_s=%.4f host_s=%.4f split_s=%.4f\n", l, ns, nmax,
+            tp[1] - tp[0], tp[2] - tp[1], tp[3] - tp[2], tp[4] - tp[3]);
   int bd = nb.total();
   c.st.max_bond_dim = std::max(c.st.max_bond_dim, bd);
   return disc;
@@ -736,38 +751,51 @@ double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, i
   int its = 0;
   bool indef = false;
   double bn = std::sqrt(std::max(0.0, dev_dot(c, bb.d(), bb.d(), n)));
+  double J = 0;
   if (prec == MPSLCC_FP64) {
     solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(c.opts.tol, 1e-14), c.opts.max_iter, prec, &its,
                  &indef);
+    // local Hylleraas value J = x.Ax - 2 x.b (the FP64 value of the final
+    // state comes from mpslcc_energy)
+    Vec ax;
+    ax.alloc(c, n);
+    A.apply(c, xb.d(), ax.d(), prec);
+    J = dev_dot(c, xb.d(), ax.d(), n) - 2.0 * dev_dot(c, xb.d(), bb.d(), n);
   } else {
-    // mixed-precision iterative refinement: residuals r = b - A x with
-    // BF16X6 products (~2^-24) and FP64 vectors, corrections from inner
-    // solves with `prec` products (BF16X3 ~2^-17; TF32 / BF16 coarser)
+    // mixed-precision iterative refinement.  A solve with `prec` products
+    // (BF16X3 ~2^-17; TF32 / BF16 coarser) from the current two-site state,
+    // then corrections against residuals r = b - A x evaluated with BF16X6
+    // products (~2^-24) and FP64 vectors
     const double inner = prec == MPSLCC_BF16X3 || prec == MPSLCC_BF16X6 ? 1e-4 : 0.05;
+    const double target = std::max(c.opts.tol, 1e-14) * bn;
     Vec r, dx, ax;
     r.alloc(c, n);
     dx.alloc(c, n);
     ax.alloc(c, n);
-    project(c, u, xb.d(), n);  // the solution lies in the range of Q_loc
-    for (int ref = 0; ref < std::max(1, c.opts.refine_steps); ++ref) {
+    solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(inner, c.opts.tol), c.opts.max_iter, prec, &its, &indef);
+    double rprev = HUGE_VAL;
+    for (int ref = 0;; ++ref) {
       A.apply(c, xb.d(), ax.d(), MPSLCC_BF16X6);
       copyv(c, r.d(), bb.d(), n);
       launch_axpy(n, -1.0, ax.d(), r.d(), c.s());
       double rn = vnorm(c, r);
-      if (rn <= std::max(c.opts.tol, 1e-14) * bn) break;
+      // done at the target, once the residual stops falling (the floor of
+      // the BF16X6 products, ~2^-24 |A| |x|), or after refine_steps
+      // corrections; x.Ax = x.b - x.r gives the local Hylleraas value
+      if (rn <= target || rn > 0.5 * rprev || ref >= c.opts.refine_steps) {
+        J = -dev_dot(c, xb.d(), bb.d(), n) - dev_dot(c, xb.d(), r.d(), n);
+        break;
+      }
+      rprev = rn;
       launch_fill(n, 0.0, dx.d(), c.s());
       int it2 = 0;
-      solve_linear(c, A, r.d(), dx.d(), dg.d(), n, std::max(inner, c.opts.tol), c.opts.max_iter, prec, &it2, &indef);
+      // the correction needs no more relative accuracy than the target asks
+      const double itol = std::min(0.5, std::max(inner, target / rn));
+      solve_linear(c, A, r.d(), dx.d(), dg.d(), n, itol, c.opts.max_iter, prec, &it2, &indef);
       its += it2;
       launch_axpy(n, 1.0, dx.d(), xb.d(), c.s());
     }
   }
-  // local Hylleraas value J = x.Ax - 2 x.b with residual-precision products
-  // (the FP64 value of the final state comes from mpslcc_energy)
-  Vec ax;
-  ax.alloc(c, n);
-  A.apply(c, xb.d(), ax.d(), rprec);
-  double J = dev_dot(c, xb.d(), ax.d(), n) - 2.0 * dev_dot(c, xb.d(), bb.d(), n);
   delete tsol;
   *its_out = its;
   *indef_out = indef;

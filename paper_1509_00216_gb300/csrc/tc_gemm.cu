@@ -44,6 +44,9 @@ struct alignas(64) TcTask {
   long long soff;
   double alpha, beta;   // mode 4: FP64 store C = alpha acc + beta C
   long long tile0;
+  int batch;            // independent products of the same shape
+  int a3d, b3d;         // operand map has the batch as third dimension (else shared)
+  long long cbatch;     // output offset between batch entries (elements)
 };
 
 namespace {
@@ -114,6 +117,37 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "[%2];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
+                                         int three) {
+  if (three) tma_load_3d(dst, map, bar, x, y, z);
+  else tma_load_2d(dst, map, bar, x, y);
+}
+
+// Tile coordinates of global tile `tile` within task T: batch entry, K split,
+// M tile and N tile.
+struct TileCoord { int b, ks, tmi, tni; };
+__device__ __forceinline__ TileCoord tile_coord(const TcTask* T, long long tile) {
+  const long long local = tile - T->tile0;
+  const long long tiles_mn = (long long)T->tm * T->tn;
+  const long long per_b = tiles_mn * T->ksplit;
+  TileCoord tc;
+  tc.b = (int)(local / per_b);
+  const long long lb = local - (long long)tc.b * per_b;
+  tc.ks = (int)(lb / tiles_mn);
+  const int r = (int)(lb - (long long)tc.ks * tiles_mn);
+  tc.tmi = r / T->tn;
+  tc.tni = r - tc.tmi * T->tn;
+  return tc;
 }
 
 __device__ __forceinline__ uint64_t sdesc(const void* p) {
@@ -342,25 +376,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
       uint32_t it = 0;
       for (long long tile = blockIdx.x; tile < total && !*s_abort; tile += gridDim.x) {
         const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
-        const long long local = tile - T->tile0;
-        const int tiles_mn = T->tm * T->tn;
-        const int ks = (int)(local / tiles_mn);
-        const int r = (int)(local - (long long)ks * tiles_mn);
-        const int tmi = r / T->tn, tni = r - (r / T->tn) * T->tn;
-        const int kt0 = ks * T->kchunk;
+        const TileCoord tc = tile_coord(T, tile);
+        const int kt0 = tc.ks * T->kchunk;
         const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
-        const int row0 = tmi * 128, col0 = tni * T->ntile;
+        const int row0 = tc.tmi * 128, col0 = tc.tni * T->ntile;
         const uint32_t bbytes = (uint32_t)T->ntile * 128u;
         for (int j = 0; j < nk; ++j, ++it) {
           const uint32_t s = it % NST, ph = (it / NST) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, err, 1)) { *s_abort = 1; break; }
           uint8_t* st = smem + s * SB;
+          const int kx = (kt0 + j) * KT;
           mbar_expect_tx(&full[s], (SPLIT ? 2u : 1u) * (A_BYTES + bbytes));
-          tma_load_2d(st, &T->ma, &full[s], (kt0 + j) * KT, row0);
-          tma_load_2d(st + A_BYTES, &T->mb, &full[s], (kt0 + j) * KT, col0);
+          tma_load(st, &T->ma, &full[s], kx, row0, tc.b, T->a3d);
+          tma_load(st + A_BYTES, &T->mb, &full[s], kx, col0, tc.b, T->b3d);
           if (SPLIT) {
-            tma_load_2d(st + STAGE_BYTES, &T->ma2, &full[s], (kt0 + j) * KT, row0);
-            tma_load_2d(st + STAGE_BYTES + A_BYTES, &T->mb2, &full[s], (kt0 + j) * KT, col0);
+            tma_load(st + STAGE_BYTES, &T->ma2, &full[s], kx, row0, tc.b, T->a3d);
+            tma_load(st + STAGE_BYTES + A_BYTES, &T->mb2, &full[s], kx, col0, tc.b, T->b3d);
           }
         }
       }
@@ -370,10 +401,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
       uint32_t it = 0, tcount = 0;
       for (long long tile = blockIdx.x; tile < total && !*s_abort; tile += gridDim.x, ++tcount) {
         const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
-        const long long local = tile - T->tile0;
-        const int tiles_mn = T->tm * T->tn;
-        const int ks = (int)(local / tiles_mn);
-        const int kt0 = ks * T->kchunk;
+        const TileCoord tc = tile_coord(T, tile);
+        const int kt0 = tc.ks * T->kchunk;
         const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
         const uint32_t buf = tcount & 1u;
         const uint32_t acc = tmem + buf * ACC_COLS;
@@ -410,12 +439,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
     uint32_t tcount = 0;
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
       const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
-      const long long local = tile - T->tile0;
-      const int tiles_mn = T->tm * T->tn;
-      const int ks = (int)(local / tiles_mn);
-      const int r = (int)(local - (long long)ks * tiles_mn);
-      const int tmi = r / T->tn, tni = r - (r / T->tn) * T->tn;
-      const int row0 = tmi * 128, col0 = tni * T->ntile;
+      const TileCoord tc = tile_coord(T, tile);
+      const int row0 = tc.tmi * 128, col0 = tc.tni * T->ntile;
       const int ntile = T->ntile;
       const uint32_t buf = tcount & 1u;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (tcount >> 1) & 1u, err, 3));
@@ -425,7 +450,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
       const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
       const bool live = row < T->m;
       long long roff = 0;
-      if (live) roff = (long long)(row / T->rpb) * T->bstride + (long long)(row % T->rpb) * T->ldc;
+      if (live)
+        roff = (long long)tc.b * T->cbatch + (long long)(row / T->rpb) * T->bstride + (long long)(row % T->rpb) * T->ldc;
       for (int cb = 0; cb < ntile; cb += 32) {
         uint32_t v[32];
         tmem_ld32(taddr + cb, v);
@@ -562,6 +588,29 @@ void encode_map(Ctx& c, CUtensorMap* map, int prec, const void* base, long rows,
   MPSLCC_REQUIRE(r == CUDA_SUCCESS, ST_CUDA, "cuTensorMapEncodeTiled failed");
 }
 
+// 3D K-major operand map: `batch` matrices of `rows` x `cols`, row pitch `ld`
+// and matrix pitch `bs` elements; box = box_rows x 128 bytes x 1 matrix.
+void encode_map3d(Ctx& c, CUtensorMap* map, int prec, const void* base, long rows, long cols, long ld, long batch,
+                  long long bs, int box_rows) {
+  const int es = esize(prec);
+  MPSLCC_REQUIRE(((uintptr_t)base & 15) == 0, ST_INTERNAL, "tensor map base not 16-byte aligned");
+  MPSLCC_REQUIRE((ld * es) % 16 == 0 && (bs * es) % 16 == 0, ST_INTERNAL,
+                 "tensor map pitches not multiples of 16 bytes");
+  MPSLCC_REQUIRE(rows >= 1 && cols >= 1 && batch >= 1 && box_rows >= 1 && box_rows <= 256 && cols <= ld &&
+                     bs >= (rows - 1) * ld + cols,
+                 ST_INTERNAL, "bad 3D tensor map extents");
+  c.check_bytes(base, ((batch - 1) * bs + (rows - 1) * ld + cols) * es, "tensor map extent");
+  cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(bs * es)};
+  cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(map, prec == MPSLCC_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           3, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  MPSLCC_REQUIRE(r == CUDA_SUCCESS, ST_CUDA, "cuTensorMapEncodeTiled (3D) failed");
+}
+
 int sm_count(Ctx& c) {
   static int n = 0;
   if (!n) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c.device);
@@ -571,20 +620,32 @@ int sm_count(Ctx& c) {
 // C (m x n, remapped rows) op= A (m x K) B (n x K)^T.  In split mode (prec
 // BF16X3) each operand row holds the hi part at +0 and the lo part at +lo_off
 // elements (lda / ldb span both); k is the length of one part.
+// One tensor-core task C = A B^T (A m x k, B n x k, K contiguous).  With
+// batch > 1 it holds `batch` products of this shape: operand X advances by
+// x_bs elements per entry (0 = shared by all entries) and C by c_bs.
 TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long ldb, int m, int n, int k, void* C,
                  int ldc, int rpb, long long bstride, int mode, int ksplit_hint, long long soff = 0,
-                 long lo_off = 0) {
+                 long lo_off = 0, int batch = 1, long long a_bs = 0, long long b_bs = 0, long long c_bs = 0) {
   TcTask t;
   std::memset(&t, 0, sizeof(t));
   const int KT = prec == MPSLCC_TF32 ? 32 : 64;
+  MPSLCC_REQUIRE(batch >= 1, ST_INTERNAL, "task batch");
+  t.batch = batch;
+  t.a3d = batch > 1 && a_bs != 0;
+  t.b3d = batch > 1 && b_bs != 0;
+  t.cbatch = batch > 1 ? c_bs : 0;
   t.ntile = (int)std::min<long>(256, (n + 15) / 16 * 16);
-  encode_map(c, &t.ma, prec, A, m, k, lda, 128);
-  encode_map(c, &t.mb, prec, B, n, k, ldb, t.ntile);
+  auto map = [&](CUtensorMap* mp, const void* base, long rows, long ld, int box, bool three, long long bs) {
+    if (three) encode_map3d(c, mp, prec, base, rows, k, ld, batch, bs, box);
+    else encode_map(c, mp, prec, base, rows, k, ld, box);
+  };
+  map(&t.ma, A, m, lda, 128, t.a3d, a_bs);
+  map(&t.mb, B, n, ldb, t.ntile, t.b3d, b_bs);
   t.split = prec == MPSLCC_BF16X3;
   if (t.split) {
     MPSLCC_REQUIRE(lo_off >= k && lo_off % 8 == 0, ST_INTERNAL, "bad split operand layout");
-    encode_map(c, &t.ma2, prec, (const char*)A + lo_off * 2, m, k, lda, 128);
-    encode_map(c, &t.mb2, prec, (const char*)B + lo_off * 2, n, k, ldb, t.ntile);
+    map(&t.ma2, (const char*)A + lo_off * 2, m, lda, 128, t.a3d, a_bs);
+    map(&t.mb2, (const char*)B + lo_off * 2, n, ldb, t.ntile, t.b3d, b_bs);
   }
   t.C = C;
   t.ldc = ldc;
@@ -609,6 +670,7 @@ TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long 
   }
   if (mode == 3) last += soff;
   if (mode == 5) last += 5 * soff;
+  last += (long long)(batch - 1) * t.cbatch;
   t.soff = soff;
   c.check_bytes(C, (last + 1) * es, "tc output");
   return t;
@@ -618,7 +680,7 @@ long long plan_tc(std::vector<TcTask>& t) {
   long long tot = 0;
   for (auto& x : t) {
     x.tile0 = tot;
-    tot += (long long)x.ksplit * x.tm * x.tn;
+    tot += (long long)std::max(1, x.batch) * x.ksplit * x.tm * x.tn;
   }
   return tot;
 }
@@ -1091,6 +1153,7 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
   t.tm = (m + 127) / 128;
   t.tn = (n + t.ntile - 1) / t.ntile;
   t.tile0 = 0;
+  t.batch = 1;
   long long tiles = (long long)t.tm * t.tn;
   cuda_check(cudaMemcpyAsync(base + o_task, &t, sizeof(t), cudaMemcpyHostToDevice, stream), "noalloc task");
   int grid = (int)std::min<long long>(tiles, 148);
@@ -1114,30 +1177,42 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
 // (FP32 accumulation), used for the environment, fusion and truncation
 // products of mixed-precision sweeps.
 // ---------------------------------------------------------------------------
+// FP64 GEMM tasks on the tensor cores: every operand is split into three
+// BF16 parts (six-block layout, A side [h h m m h l], B side [h m m h l h])
+// and multiplied by the plain BF16 kernel over K' = 6 K, with an FP64
+// alpha/beta epilogue (about 2^-24 relative).  A task's batch stays one
+// tensor-core task: batched operands are converted to contiguous
+// [batch][rows][6 K] stacks read through 3D tensor maps.
 void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
   if (tasks.empty()) return;
   const double th0 = c.opts.verbose >= 2 ? wall_seconds() : 0.0;
   struct Key {
     const double* p;
-    int rows, cols, ld, trans;
+    int rows, cols, ld, trans, nb;
+    long long st;
     bool operator<(const Key& o) const {
       if (p != o.p) return p < o.p;
       if (rows != o.rows) return rows < o.rows;
       if (cols != o.cols) return cols < o.cols;
       if (ld != o.ld) return ld < o.ld;
-      return trans < o.trans;
+      if (trans != o.trans) return trans < o.trans;
+      if (nb != o.nb) return nb < o.nb;
+      return st < o.st;
     }
   };
   std::map<Key, long> opoff;
   std::vector<ConvTask> cv;
   long tot = 0;
-  auto add_op = [&](const double* p, int rows, int cols, int ld, int trans, int side) -> long {
-    Key k{p, rows, cols, ld, trans + 2 * side};
+  // operand `rows` x `cols` (K) read from p (transposed if trans), nb batch
+  // entries st elements apart; returns its element offset in the scratch
+  auto add_op = [&](const double* p, int rows, int cols, int ld, int trans, int side, int nb,
+                    long long st) -> long {
+    Key k{p, rows, cols, ld, trans + 2 * side, nb, st};
     auto it = opoff.find(k);
     if (it != opoff.end()) return it->second;
     long off = tot;
     const long kp = pad8(cols);
-    tot += pad8((long)rows * 6 * kp);
+    tot += pad8((long)nb * rows * 6 * kp);
     ConvTask t;
     std::memset(&t, 0, sizeof(t));
     t.src = p;
@@ -1146,7 +1221,9 @@ void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
     t.cols = cols;
     t.src_ld = ld;
     t.dst_ld = (int)(6 * kp);
-    t.batch = 1;
+    t.batch = nb;
+    t.s_src = st;
+    t.s_dst = (long long)rows * 6 * kp;
     t.pattern = side;
     t.soff = kp;
     t.trans = trans;
@@ -1154,19 +1231,18 @@ void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
     opoff[k] = off;
     return off;
   };
-  struct Job { long ao, bo; double* C; int m, n, k, ldc; double alpha, beta; };
+  struct Job { long ao, bo; double* C; int m, n, k, ldc; double alpha, beta; int nb; bool a3, b3; long long sC; };
   std::vector<Job> jobs;
+  double fl = 0;
   for (const auto& t : tasks) {
     if (t.m <= 0 || t.n <= 0 || t.batch <= 0) continue;
     MPSLCC_REQUIRE(t.k > 0 && t.ksplit <= 1, ST_INTERNAL, "tensor-core FP64 task shape");
     const bool ta = t.flags & GEMM_TA, tb = t.flags & GEMM_TB;
-    for (int b = 0; b < t.batch; ++b) {
-      const double* A = t.A + (long long)b * t.sA;
-      const double* B = t.B + (long long)b * t.sB;
-      long ao = add_op(A, t.m, t.k, t.lda, ta ? 1 : 0, 2);   // op(A): m x k
-      long bo = add_op(B, t.n, t.k, t.ldb, tb ? 0 : 1, 3);   // op(B)^T: n x k
-      jobs.push_back({ao, bo, t.C + (long long)b * t.sC, t.m, t.n, t.k, t.ldc, t.alpha, t.beta});
-    }
+    const bool a3 = t.batch > 1 && t.sA != 0, b3 = t.batch > 1 && t.sB != 0;
+    long ao = add_op(t.A, t.m, t.k, t.lda, ta ? 1 : 0, 2, a3 ? t.batch : 1, a3 ? t.sA : 0);  // op(A): m x k
+    long bo = add_op(t.B, t.n, t.k, t.ldb, tb ? 0 : 1, 3, b3 ? t.batch : 1, b3 ? t.sB : 0);  // op(B)^T: n x k
+    jobs.push_back({ao, bo, t.C, t.m, t.n, t.k, t.ldc, t.alpha, t.beta, t.batch, a3, b3, t.sC});
+    fl += 2.0 * t.m * t.n * t.k * t.batch;
   }
   if (jobs.empty()) return;
   c.scratch_tc.ensure(&c, std::max<long>(tot, 8) * 2);
@@ -1178,8 +1254,9 @@ void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
   tt.reserve(jobs.size());
   for (const auto& j : jobs) {
     const long kp = pad8(j.k);
+    const long long sa = (long long)j.m * 6 * kp, sb = (long long)j.n * 6 * kp;
     TcTask t = make_task(c, MPSLCC_BF16, base + j.ao * 2, 6 * kp, base + j.bo * 2, 6 * kp, j.m, j.n, (int)(6 * kp),
-                         j.C, j.ldc, 1 << 30, 0, 4, 1);
+                         j.C, j.ldc, 1 << 30, 0, 4, 1, 0, 0, j.nb, j.a3 ? sa : 0, j.b3 ? sb : 0, j.sC);
     t.alpha = j.alpha;
     t.beta = j.beta;
     tt.push_back(t);
@@ -1192,15 +1269,13 @@ void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
   cuda_check(cudaMemsetAsync(c.tc_err.p, 0, 16, c.s()), "tc err zero");
   const double th1 = c.opts.verbose >= 2 ? wall_seconds() : 0.0;
   launch_tc(c, MPSLCC_BF16, (const TcTask*)c.tc_gemm_tasks.p, (int)tt.size(), tiles, (int*)c.tc_err.p);
-  double fl = 0;
-  for (const auto& j : jobs) fl += 2.0 * j.m * j.n * j.k;
   c.st.tc_gemm_flops += fl;
   check_err(c, c.tc_err);
   if (c.opts.verbose >= 2) {
     long conv_elems = 0;
-    for (const auto& t : cv) conv_elems += (long)t.rows * t.cols;
-    fprintf(stderr, "[fp64-tc] tasks=%zu jobs=%zu conv=%zu conv_elems=%ld flops=%.3e host_s=%.4f total_s=%.4f\n",
-            tasks.size(), jobs.size(), cv.size(), conv_elems, fl, th1 - th0, wall_seconds() - th0);
+    for (const auto& t : cv) conv_elems += (long)t.rows * t.cols * t.batch;
+    fprintf(stderr, "[fp64-tc] tasks=%zu jobs=%zu conv=%zu conv_elems=%ld flops=%.3e tiles=%lld host_s=%.4f total_s=%.4f\n",
+            tasks.size(), jobs.size(), cv.size(), conv_elems, fl, tiles, th1 - th0, wall_seconds() - th0);
   }
 }
 
