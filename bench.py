@@ -42,7 +42,9 @@ def parse():
     ap.add_argument("--config", type=int, default=3)
     ap.add_argument("--M0", type=int, default=None)
     ap.add_argument("--M1", type=int, default=None)
-    ap.add_argument("--dmrg-sweeps", type=int, default=4)
+    ap.add_argument("--dmrg-sweeps", type=int, default=8)
+    ap.add_argument("--dmrg-init", choices=["product", "random"], default="product",
+                    help="reference start: lowest-h_pp determinant or random MPS")
     ap.add_argument("--prec", default="bf16x3", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -258,7 +260,8 @@ def gpu_arm(args, rank, world, local_rank):
     M0 = args.M0 or c["M0"]
     M1 = args.M1 or c["M1"]
     prec = PREC[args.prec]
-    ctx = mp.Context(device=local_rank, prec=prec, tol=1e-8, max_iter=60, torch_memory=True)
+    ctx = mp.Context(device=local_rank, prec=prec, tol=1e-8, max_iter=60, torch_memory=True,
+                     init_guess=1 if args.dmrg_init == "product" else 0)
     ctx.build_mpo(c["h"], c["V"], c["n_alpha"] + c["n_beta"], 0)
     ctx.set_spaces(c["n_core"], c["n_active"])
     E0 = ctx.dmrg_reference(M0, args.dmrg_sweeps)

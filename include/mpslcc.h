@@ -96,6 +96,9 @@ typedef struct {
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, size_t bytes, void* user);
   void* alloc_user;
+  int init_guess;        /* reference start: 0 = random MPS over all allowed
+                            sectors (opts.seed), 1 = product state filling
+                            the active orbitals of lowest h_pp            */
 } mpslcc_opts;
 
 typedef struct {

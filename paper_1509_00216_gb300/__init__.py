@@ -39,7 +39,8 @@ class Opts(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("prec", C.c_int), ("tol", C.c_double),
                 ("max_iter", C.c_int), ("solver", C.c_int), ("davidson_max_subspace", C.c_int),
                 ("refine_steps", C.c_int), ("seed", C.c_ulonglong), ("verbose", C.c_int),
-                ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p)]
+                ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p),
+                ("init_guess", C.c_int)]
 
 
 class Energies(C.Structure):
@@ -139,7 +140,7 @@ class Context:
     allocator on the current torch stream."""
 
     def __init__(self, device=0, prec=FP64, tol=1e-10, max_iter=200, seed=7, verbose=0, refine_steps=4,
-                 davidson_max_subspace=24, torch_memory=False):
+                 davidson_max_subspace=24, torch_memory=False, init_guess=0):
         L = lib()
         o = Opts()
         L.mpslcc_default_opts(C.byref(o))
@@ -151,6 +152,7 @@ class Context:
         o.verbose = verbose
         o.refine_steps = refine_steps
         o.davidson_max_subspace = davidson_max_subspace
+        o.init_guess = init_guess
         self._cb = None
         if torch_memory and device >= 0:
             import torch

@@ -30,7 +30,7 @@ def _compile(src: str) -> str:
     deps.append(os.path.join(ROOT, "include", "mpslcc.h"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
-    cmd = [_nvcc(), "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
+    cmd = [_nvcc(), "-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-Xcompiler", "-Wall",
            "-I" + os.path.join(ROOT, "include"), "-I" + CSRC, *ARCH, "-c", srcp, "-o", obj]
     if src.endswith(".cpp"):
         cmd[1:1] = ["-x", "cu"]
@@ -46,7 +46,7 @@ def build(verbose: bool = False) -> str:
         objs = list(ex.map(_compile, SOURCES))
     if os.path.exists(OUT) and os.path.getmtime(OUT) >= max(os.path.getmtime(o) for o in objs):
         return OUT
-    cmd = [_nvcc(), "-shared", *ARCH, "-o", OUT, *objs, "-lcusolver", "-lcublas", "-lcudart"]
+    cmd = [_nvcc(), "-shared", *ARCH, "-o", OUT, *objs, "-lcusolver", "-lcublas", "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

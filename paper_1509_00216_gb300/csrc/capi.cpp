@@ -93,6 +93,7 @@ void mpslcc_default_opts(mpslcc_opts* o) {
   o->solver = 2;
   o->davidson_max_subspace = 24;
   o->refine_steps = 4;
+  o->init_guess = 0;
   o->seed = 7;
   o->verbose = 0;
 }
@@ -106,6 +107,7 @@ mpslcc_status mpslcc_create(mpslcc_ctx** out, const mpslcc_opts* opts) {
   else mpslcc_default_opts(&ctx->c.opts);
   mpslcc_status st = guard(ctx, [&](Ctx& c) {
     MPSLCC_REQUIRE(c.opts.prec >= MPSLCC_FP64 && c.opts.prec <= MPSLCC_BF16X6, ST_ARG, "opts.prec out of range");
+    MPSLCC_REQUIRE(c.opts.init_guess == 0 || c.opts.init_guess == 1, ST_ARG, "opts.init_guess must be 0 or 1");
     c.device = c.opts.device;
     c.host_only = c.device < 0;
     if (c.host_only) return;

@@ -5,9 +5,11 @@
 // the local matrix is indefinite).  After each local solve the two-site
 // tensor is split by the density-matrix eigendecomposition (FP64 cuSOLVER)
 // keeping at most M states, and the environments are renormalised.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <random>
+#include <thread>
 
 #include "engine.hpp"
 
@@ -373,7 +375,8 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
   mark(1);
   // FP64 eigendecompositions (cuSOLVER), eigenvalues ascending.  The
   // sectors are independent: they run concurrently on NEIG side streams,
-  // largest first, each stream with its own handle and workspace.
+  // largest first, each stream with its own handle, workspace and host
+  // thread.
   if (!c.eig_solver[0]) {
     for (int s = 0; s < Ctx::NEIG; ++s) {
       cuda_check(cudaStreamCreateWithFlags(&c.eig_stream[s], cudaStreamNonBlocking), "eig stream");
@@ -386,29 +389,51 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
   std::vector<int> order(ns);
   for (int i = 0; i < ns; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return nd[a] > nd[b]; });
-  int lwork[Ctx::NEIG] = {0};
+  int lwork = 0;
   for (int t = 0; t < ns; ++t) {
-    int i = order[t], sidx = t % Ctx::NEIG, lw = 0;
-    cusolverDnDsyevd_bufferSize(c.eig_solver[sidx], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i],
+    int i = order[t], lw = 0;
+    cusolverDnDsyevd_bufferSize(c.eig_solver[0], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i],
                                 rho.d() + roff[i], nd[i], w.d() + woff[i], &lw);
-    lwork[sidx] = std::max(lwork[sidx], lw);
+    lwork = std::max(lwork, lw);
   }
-  for (int sidx = 0; sidx < Ctx::NEIG; ++sidx) {
-    c.eig_ws[sidx].ensure(&c, (size_t)std::max(lwork[sidx], 1) * sizeof(double));
+  const int nthreads = std::max(1, std::min(Ctx::NEIG, ns));
+  for (int sidx = 0; sidx < nthreads; ++sidx) {
+    c.eig_ws[sidx].ensure(&c, (size_t)std::max(lwork, 1) * sizeof(double));
     c.eig_inf[sidx].ensure(&c, sizeof(int) * 4);
+  }
+  for (int i = 0; i < ns; ++i) {
+    c.check_range(rho.d() + roff[i], 0, (long long)nd[i] * nd[i] - 1, "eigh matrix");
+    c.check_range(w.d() + woff[i], 0, nd[i] - 1, "eigh values");
   }
   cuda_check(cudaEventRecord(c.eig_fork, c.s()), "eig fork");
   for (int sidx = 0; sidx < Ctx::NEIG; ++sidx) cudaStreamWaitEvent(c.eig_stream[sidx], c.eig_fork, 0);
-  for (int t = 0; t < ns; ++t) {
-    int i = order[t], sidx = t % Ctx::NEIG;
-    c.check_range(rho.d() + roff[i], 0, (long long)nd[i] * nd[i] - 1, "eigh matrix");
-    c.check_range(w.d() + woff[i], 0, nd[i] - 1, "eigh values");
-    cusolverStatus_t st = cusolverDnDsyevd(c.eig_solver[sidx], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                           nd[i], rho.d() + roff[i], nd[i], w.d() + woff[i], c.eig_ws[sidx].d(),
-                                           lwork[sidx], (int*)c.eig_inf[sidx].p);
-    MPSLCC_REQUIRE(st == CUSOLVER_STATUS_SUCCESS, ST_CUDA, "cusolverDnDsyevd failed");
-    c.st.kernel_launches++;
-  }
+  // cusolverDnDsyevd blocks its calling thread on host-side steps, so every
+  // stream gets its own host thread; the threads take sectors largest first
+  std::atomic<int> next{0};
+  std::vector<int> bad(nthreads, 0);
+  auto worker = [&](int sidx) {
+    if (cudaSetDevice(c.device) != cudaSuccess) {
+      bad[sidx] = 1;
+      return;
+    }
+    for (;;) {
+      const int t = next.fetch_add(1);
+      if (t >= ns) break;
+      const int i = order[t];
+      if (cusolverDnDsyevd(c.eig_solver[sidx], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i],
+                           rho.d() + roff[i], nd[i], w.d() + woff[i], c.eig_ws[sidx].d(), lwork,
+                           (int*)c.eig_inf[sidx].p) != CUSOLVER_STATUS_SUCCESS) {
+        bad[sidx] = 1;
+        break;
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int sidx = 1; sidx < nthreads; ++sidx) pool.emplace_back(worker, sidx);
+  worker(0);
+  for (auto& th : pool) th.join();
+  for (int sidx = 0; sidx < nthreads; ++sidx) MPSLCC_REQUIRE(!bad[sidx], ST_CUDA, "cusolverDnDsyevd failed");
+  c.st.kernel_launches += ns;
   for (int sidx = 0; sidx < Ctx::NEIG; ++sidx) {
     cuda_check(cudaEventRecord(c.eig_ev[sidx], c.eig_stream[sidx]), "eig join");
     cudaStreamWaitEvent(c.s(), c.eig_ev[sidx], 0);
@@ -534,6 +559,60 @@ void bind(Ctx& c, Family& F, MPS* bra, int mpo, MPS* ket) {
 }  // namespace
 
 // ---------------------------------------------------------------------------
+// Reference start from one determinant: core orbitals doubly occupied,
+// virtual ones empty, and the active electrons in the active orbitals of
+// lowest h_pp (doubly occupied first, the spin excess as single up or down
+// electrons).  A product state: every bond holds one sector of dimension 1.
+void init_product_mps(Ctx& c, MPS& m) {
+  const int k = c.k;
+  const int na = (c.n_elec + c.two_sz) / 2 - c.n_core, nb = (c.n_elec - c.two_sz) / 2 - c.n_core;
+  MPSLCC_REQUIRE(na >= 0 && nb >= 0 && na <= c.n_active && nb <= c.n_active && (c.n_elec + c.two_sz) % 2 == 0,
+                 ST_ARG, "no determinant with the requested electron number / spin fits the orbital partition");
+  std::vector<int> act;
+  for (int p = c.n_core; p < c.n_core + c.n_active; ++p) act.push_back(p);
+  std::stable_sort(act.begin(), act.end(), [&](int a, int b) { return c.h[(size_t)a * k + a] < c.h[(size_t)b * k + b]; });
+  std::vector<int> occ(k, 0);
+  for (int p = 0; p < c.n_core; ++p) occ[p] = 3;
+  for (int i = 0; i < (int)act.size(); ++i) occ[act[i]] = (i < na ? 1 : 0) + (i < nb ? 2 : 0);
+  m = MPS();
+  m.k = k;
+  m.target = QN(c.n_elec, c.two_sz);
+  m.mask.resize(k);
+  for (int p = 0; p < k; ++p) {
+    if (p < c.n_core) m.mask[p] = {3};
+    else if (p >= c.n_core + c.n_active) m.mask[p] = {0};
+    else m.mask[p] = {0, 1, 2, 3};
+  }
+  m.bond.assign(k + 1, Sectors());
+  QN q(0, 0);
+  for (int b = 0; b <= k; ++b) {
+    m.bond[b].q.push_back(q);
+    m.bond[b].d.push_back(1);
+    if (b < k) q = q + LOCAL_Q[occ[b]];
+  }
+  MPSLCC_REQUIRE(m.bond[k].q[0] == m.target, ST_INTERNAL, "product state misses the target quantum numbers");
+  m.site.clear();
+  m.site.resize(k);
+  for (int p = 0; p < k; ++p) {
+    long tot;
+    std::vector<long> off = layout_offsets(m, p, 1, &tot);
+    Fused FR = fuse_right(m.mask[p], m.bond[p + 1]);
+    std::vector<double> host(std::max(tot, 1L), 0.0);
+    const int f = FR.find(m.bond[p].q[0]);
+    MPSLCC_REQUIRE(f >= 0, ST_INTERNAL, "product state sector");
+    const Piece* pc = FR.piece(f, 0, occ[p]);
+    MPSLCC_REQUIRE(pc != nullptr, ST_INTERNAL, "product state piece");
+    host[off[0] + pc->off] = 1.0;
+    DBuf d;
+    d.alloc(&c, host.size() * sizeof(double));
+    cuda_check(cudaMemcpyAsync(d.p, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, c.s()),
+               "upload mps");
+    cuda_check(cudaStreamSynchronize(c.s()), "upload mps sync");
+    set_site_rf(c, m, p, std::move(d));
+  }
+  m.present = true;
+}
+
 void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed) {
   int k = c.k;
   m = MPS();
@@ -647,7 +726,8 @@ void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed
 double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
   int k = c.k;
   const bool mixed = c.opts.prec != MPSLCC_FP64;
-  init_random_mps(c, c.phi0, std::min(M0, 16), true, c.opts.seed);
+  if (c.opts.init_guess == 1) init_product_mps(c, c.phi0);
+  else init_random_mps(c, c.phi0, std::min(M0, 16), true, c.opts.seed);
   double E = 0;
   bool all_conv = true;
   // one half-sweep of two-site Davidson updates (Eq. EH): products and the

@@ -899,11 +899,6 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     t.soff = pad8(t.cols);
     S->xconv.push_back(t);
   }
-  long long base = 0;
-  for (size_t bi = 0; bi < nbk; ++bi) {
-    int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
-    base += (long long)((lb + 127) / 128) * ((rb + 255) / 256);
-  }
   const long long target = 2LL * sm_count(c);
   for (int v = 0; v < (six ? 2 : 1); ++v) {
     // v = 0: the layout's own precision; v = 1: BF16X6 (plain BF16 kernel over
@@ -930,13 +925,23 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
       // algorithmic bytes: operands and result once, per piece read or written
       S->bytes1[v] += (double)es * pcs * ((double)st.nw * rb * rk + (double)lk * rk + (double)st.nw * rb * lk);
     }
-    // phase 2: sigma = Lcat Tt^T, split over K
+    // phase 2: sigma = Lcat Tt^T, split over K so that every tile carries
+    // about the same number of K steps (a balanced persistent schedule)
+    long long work = 0;
+    for (size_t bi = 0; bi < nbk; ++bi) {
+      if (S->K8[bi] == 0) continue;
+      const int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+      const long kk = v == 1 ? sp * S->K8[bi] : S->K8[bi];
+      const long nt = std::min<long>(256, (rb + 15) / 16 * 16);
+      work += (long long)((lb + 127) / 128) * ((rb + nt - 1) / nt) * ((kk + 63) / 64);
+    }
+    const long long kper = std::max(4LL, (work + 4 * target - 1) / (4 * target));
     for (size_t bi = 0; bi < nbk; ++bi) {
       if (S->K8[bi] == 0) continue;
       int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
       const long pitch = sp * S->K8[bi];
       const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
-      int ks = (int)std::max(1LL, (target + base - 1) / std::max(1LL, base));
+      int ks = (int)std::max(1LL, (((long long)kk + 63) / 64 + kper - 1) / kper);
       t2.push_back(make_task(c, kp, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, pitch,
                              (char*)S->tt.p + (size_t)S->tt_off[bi] * es, pitch, lb, rb, kk,
                              (float*)S->y.p + P.off_b[bi], rb, 1 << 30, 0, 0, ks, 0,

@@ -99,6 +99,19 @@ def test_config0_energies_at_exact_bond_dimension(mpslcc):
     assert abs(e["overlap01"]) <= 1e-8
 
 
+def test_product_start_reaches_exact_reference(mpslcc):
+    """Starting the reference from the lowest-h_pp determinant (a bond
+    dimension 1 product state), two-site sweeps grow the bonds to the exact
+    M0 = 16 and reach the determinant-space E0 of the L=8 chain."""
+    g = GOLDEN["hubbard1d_L8_U4"]
+    c = synth.config(0)
+    with mpslcc.Context(device=0, tol=1e-11, init_guess=1) as ctx:
+        ctx.build_mpo(c["h"], c["V"], 8, 0)
+        ctx.set_spaces(c["n_core"], c["n_active"])
+        E0 = ctx.dmrg_reference(16, 4)
+    assert abs(E0 - g["E0"]) <= ENERGY_TOL, (E0, g["E0"])
+
+
 @pytest.mark.parametrize("t,U", [(1.0, 4.0), (1.0, 1.0)])
 def test_dimer_lcc_closed_form(mpslcc, t, U):
     """E0 = -2t + U/2, E2 = -U^2/(16t), E3 = 0 for the bonding/antibonding
