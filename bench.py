@@ -47,6 +47,8 @@ def parse():
                     help="reference start: lowest-h_pp determinant or random MPS")
     ap.add_argument("--prec", default="bf16x3", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-sweep", action="store_true",
+                    help="skip the FP64 comparison sweep (same states, plain FP64 path)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="profiling mode: N sigma products at the middle position inside NVTX range 'sigma'")
@@ -357,6 +359,28 @@ def gpu_arm(args, rank, world, local_rank):
     clk_s = clk.summary()
     if clk_s:
         line["clocks"] = clk_s
+    if not args.no_fp64_sweep and prec != 0:
+        # the same sweep on the plain FP64 path (DFMA GEMMs), from the same
+        # reference and first-order states, outside the timed region
+        p0, p1 = ctx.export_mps(0), ctx.export_mps(1)
+        ctx.close()
+        c64 = mp.Context(device=local_rank, prec=mp.FP64, tol=1e-8, max_iter=60, torch_memory=True)
+        c64.build_mpo(c["h"], c["V"], c["n_alpha"] + c["n_beta"], 0)
+        c64.set_spaces(c["n_core"], c["n_active"])
+        c64.load_mps(0, p0)
+        c64.dmrg_reference(M0, 0)
+        c64.load_mps(1, p1)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        c64.lcc_sweep(M1, 1)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f64_s = f0.elapsed_time(f1) * 1e-3
+        c64.close()
+        line["fp64_sweep_s"] = f64_s
+        line["sweep_speedup_vs_fp64"] = f64_s / (dev_s / args.steps)
     ctx.close()
     if rank == 0:
         if not args.no_cpu_baseline:

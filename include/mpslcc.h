@@ -173,7 +173,9 @@ mpslcc_status mpslcc_set_spaces(mpslcc_ctx* ctx, int n_core, int n_active);
 /* Eq. EH: two-site DMRG for the reference Phi0 (lowest eigenvector of H0 in
    the reference class: core sites fixed to |up dn>, virtual sites to |0>),
    bond dimension M0, n_sweeps left-right-left sweeps, Davidson local solver.
-   Writes E0 = <Phi0|H|Phi0>.  E_NOCONV if a local solve hit max_iter. */
+   Writes E0 = <Phi0|H|Phi0>.  n_sweeps = 0 keeps a reference loaded by
+   mpslcc_load_mps(0) and only evaluates its E0 in FP64 (E_STATE if none is
+   loaded).  E_NOCONV if a local solve hit max_iter. */
 mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, double* E0_out);
 
 /* Eq. 1 (n = 1) in projector form: optimise Phi1 (bond dimension M1) by

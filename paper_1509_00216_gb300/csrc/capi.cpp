@@ -232,12 +232,18 @@ mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, doubl
   return guard(ctx, [&](Ctx& c) {
     need_device(c);
     MPSLCC_REQUIRE(c.have_mpo, ST_STATE, "build_mpo first");
-    MPSLCC_REQUIRE(M0 >= 1 && n_sweeps >= 1, ST_ARG, "M0 and n_sweeps must be positive");
+    MPSLCC_REQUIRE(M0 >= 1 && n_sweeps >= 0, ST_ARG, "M0 must be positive and n_sweeps non-negative");
     cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
-    reset_families(c);
-    c.phi1 = MPS();
-    c.have_E2 = c.e3_valid = false;
-    double E = dmrg_reference(c, M0, n_sweeps);
+    double E;
+    if (n_sweeps == 0) {
+      MPSLCC_REQUIRE(c.phi0.present, ST_STATE, "n_sweeps = 0 evaluates a loaded reference: load_mps(0) first");
+      E = reference_energy_fp64(c);
+    } else {
+      reset_families(c);
+      c.phi1 = MPS();
+      c.have_E2 = c.e3_valid = false;
+      E = dmrg_reference(c, M0, n_sweeps);
+    }
     if (E0_out) *E0_out = E;
   });
 }

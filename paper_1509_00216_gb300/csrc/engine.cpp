@@ -673,20 +673,40 @@ void two_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long
   }
 }
 
-void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P) {
+void build_fused_ahead(Ctx& c, Family& F, int l, bool right_side, FusedAhead& A) {
+  std::vector<QN> mb, mk;
+  std::vector<long> ob, ok;
+  long nb = 0, nk = 0;
+  two_site_middle(*F.bra, l, mb, ob, nb);
+  two_site_middle(*F.ket, l, mk, ok, nk);
+  A.l = -1;
+  if (right_side) make_right_fused(c, F, l + 1, mb, mk, A.rf);
+  else make_left_fused(c, F, l, mb, mk, A.lf);
+  A.l = l;
+  A.right = right_side;
+}
+
+void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead) {
   ensure_envs(c, F, l);
   P.l = l;
   P.fam = &F;
   two_site_middle(*F.bra, l, P.mid_b, P.off_b, P.nb);
   two_site_middle(*F.ket, l, P.mid_k, P.off_k, P.nk);
-  {
+  const bool have_l = ahead && ahead->l == l && !ahead->right;
+  const bool have_r = ahead && ahead->l == l && ahead->right;
+  if (have_l) {
+    P.lf = std::move(ahead->lf);
+  } else {
     StageTimer tm(c, &c.st.t_fuse_left);
     make_left_fused(c, F, l, P.mid_b, P.mid_k, P.lf);
   }
-  {
+  if (have_r) {
+    P.rf = std::move(ahead->rf);
+  } else {
     StageTimer tm(c, &c.st.t_fuse_right);
     make_right_fused(c, F, l + 1, P.mid_b, P.mid_k, P.rf);
   }
+  if (ahead) ahead->l = -1;
   const LeftFused& lf = P.lf;
   const RightFused& rf = P.rf;
   P.tt_off.assign(P.mid_b.size(), 0);

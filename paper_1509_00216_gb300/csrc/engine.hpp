@@ -142,6 +142,18 @@ struct RightFused {
   long size = 0;
 };
 
+// Fused operator of one side of two-site position l, built ahead of time
+// (while the truncation at the neighbouring position runs): the right side
+// R' of site l+1 during a left-to-right sweep, the left side L' of site l
+// during a right-to-left sweep.  Neither depends on the sites that
+// truncation changes.
+struct FusedAhead {
+  int l = -1;
+  bool right = false;  // holds rf (else lf)
+  LeftFused lf;
+  RightFused rf;
+};
+
 // Two-site sigma plan at position l.
 struct SigmaPlan {
   int l = -1;
@@ -276,7 +288,8 @@ void env_update_left(Ctx& c, Family& F, int p, const LeftFused& lf);
 void env_update_right(Ctx& c, Family& F, int p, const RightFused& rf);
 
 void two_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long>& off, long& n);
-void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P);
+void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead = nullptr);
+void build_fused_ahead(Ctx& c, Family& F, int l, bool right_side, FusedAhead& A);
 void sigma_apply(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec);
 void sigma_diag(Ctx& c, SigmaPlan& P, double* diag);
 void form_two_site(Ctx& c, MPS& m, int l, double* psi);   // psi in m's middle layout
@@ -297,5 +310,6 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps);
 double lcc_sweeps(Ctx& c, int M1, int n_sweeps);
 void compute_e3(Ctx& c);
 void compute_energies(Ctx& c);
+double reference_energy_fp64(Ctx& c);
 
 }  // namespace mpslcc

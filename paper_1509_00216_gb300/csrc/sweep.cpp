@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <random>
 #include <thread>
 
@@ -317,7 +318,10 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
 }
 
 // Split the two-site vector at position l of MPS m keeping <= M states.
-double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_right) {
+// The optional `overlap` runs on the calling thread, enqueueing work on the
+// main stream, while the density-matrix eigensolvers run on side streams.
+double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_right,
+                const std::function<void()>& overlap = {}) {
   std::vector<QN> mid;
   std::vector<long> off;
   long n_loc;
@@ -429,8 +433,18 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     }
   };
   std::vector<std::thread> pool;
-  for (int sidx = 1; sidx < nthreads; ++sidx) pool.emplace_back(worker, sidx);
-  worker(0);
+  if (overlap) {
+    for (int sidx = 0; sidx < nthreads; ++sidx) pool.emplace_back(worker, sidx);
+    try {
+      overlap();
+    } catch (...) {
+      for (auto& th : pool) th.join();
+      throw;
+    }
+  } else {
+    for (int sidx = 1; sidx < nthreads; ++sidx) pool.emplace_back(worker, sidx);
+    worker(0);
+  }
   for (auto& th : pool) th.join();
   for (int sidx = 0; sidx < nthreads; ++sidx) MPSLCC_REQUIRE(!bad[sidx], ST_CUDA, "cusolverDnDsyevd failed");
   c.st.kernel_launches += ns;
@@ -891,6 +905,10 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
     bind(c, c.f10, &c.phi1, MPO_H, &c.phi0);
     bind(c, c.s10, &c.phi1, MPO_ID, &c.phi0);
   }
+  // a loaded Phi1 (or Phi0) leaves the families unbound
+  if (!c.f11.bra) bind(c, c.f11, &c.phi1, MPO_H0, &c.phi1);
+  if (!c.f10.bra) bind(c, c.f10, &c.phi1, MPO_H, &c.phi0);
+  if (!c.s10.bra) bind(c, c.s10, &c.phi1, MPO_ID, &c.phi0);
   c.e3_valid = false;
   c.e_valid = false;
   c.u11.L.clear();
@@ -901,6 +919,7 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
   // right-hand side and residuals: BF16X6 products in mixed precision
   const int rprec = mixed ? MPSLCC_BF16X6 : MPSLCC_FP64;
   double J = 0, E2 = 0;
+  FusedAhead ahead[3];
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
@@ -915,9 +934,9 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
         SigmaPlan P11, P10, PS;
         {
           StageTimer tm(c, &c.st.t_plan);
-          make_sigma_plan(c, c.f11, l, P11);
-          make_sigma_plan(c, c.f10, l, P10);
-          make_sigma_plan(c, c.s10, l, PS);
+          make_sigma_plan(c, c.f11, l, P11, &ahead[0]);
+          make_sigma_plan(c, c.f10, l, P10, &ahead[1]);
+          make_sigma_plan(c, c.s10, l, PS, &ahead[2]);
           if (prec != MPSLCC_FP64) tc_prepare(c, P11, MPSLCC_BF16X3);
         }
         DBuf xb;
@@ -928,7 +947,16 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
         double disc;
         {
           StageTimer tm(c, &c.st.t_trunc);
-          disc = truncate(c, c.phi1, l, xb.d(), M1, right);
+          // the next position's fused operator on the side this truncation
+          // leaves alone is built while the eigensolvers run
+          const int ln = right ? l + 1 : l - 1;
+          std::function<void()> next;
+          if (ln >= 0 && ln <= k - 2)
+            next = [&c, &ahead, ln, right]() {
+              Family* fams[3] = {&c.f11, &c.f10, &c.s10};
+              for (int fi = 0; fi < 3; ++fi) build_fused_ahead(c, *fams[fi], ln, right, ahead[fi]);
+            };
+          disc = truncate(c, c.phi1, l, xb.d(), M1, right, next);
         }
         c.max_disc = std::max(c.max_disc, disc);
         for (Family* F : {&c.f11, &c.f10, &c.s10}) {
@@ -985,6 +1013,19 @@ double expect_fp64(Ctx& c, MPS* bra, int mpo, MPS* ket) {
   form_two_site(c, *ket, 0, xk.d());
   sigma_apply(c, P, xk.d(), y.d(), MPSLCC_FP64);
   return dev_dot(c, xb.d(), y.d(), P.nb);
+}
+
+// E0 = <Phi0|H0|Phi0> / <Phi0|Phi0> of the current (loaded) reference in FP64;
+// equal to <Phi0|H|Phi0> / <Phi0|Phi0> since U has no block inside the
+// reference class.
+double reference_energy_fp64(Ctx& c) {
+  double e = expect_fp64(c, &c.phi0, MPO_H0, &c.phi0);
+  double nn = expect_fp64(c, &c.phi0, MPO_ID, &c.phi0);
+  MPSLCC_REQUIRE(nn > 0, ST_STATE, "reference has zero norm");
+  c.E0 = e / nn;
+  c.have_E0 = true;
+  c.e_valid = c.e3_valid = false;
+  return c.E0;
 }
 
 // FP64 energies of the current first-order state (Eq. 1b, Eq. 2 with n = 1):

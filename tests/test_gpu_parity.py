@@ -112,6 +112,30 @@ def test_product_start_reaches_exact_reference(mpslcc):
     assert abs(E0 - g["E0"]) <= ENERGY_TOL, (E0, g["E0"])
 
 
+def test_resume_from_exported_states(mpslcc):
+    """Exported Phi0 and Phi1 load into a fresh context (a checkpoint): zero
+    reference sweeps re-evaluate E0, and further LCC sweeps from the loaded
+    first-order state reach the determinant-space energies."""
+    g = GOLDEN["hubbard1d_L8_U4"]
+    c = synth.config(0)
+    with mpslcc.Context(device=0, tol=1e-11) as ctx:
+        ctx.build_mpo(c["h"], c["V"], 8, 0)
+        ctx.set_spaces(c["n_core"], c["n_active"])
+        E0 = ctx.dmrg_reference(16, 3)
+        ctx.lcc_sweep(256, 1)
+        p0, p1 = ctx.export_mps(0), ctx.export_mps(1)
+    with mpslcc.Context(device=0, tol=1e-11) as ctx:
+        ctx.build_mpo(c["h"], c["V"], 8, 0)
+        ctx.set_spaces(c["n_core"], c["n_active"])
+        ctx.load_mps(0, p0)
+        assert abs(ctx.dmrg_reference(16, 0) - E0) <= 1e-12
+        ctx.load_mps(1, p1)
+        ctx.lcc_sweep(256, 2)
+        e = ctx.energy()
+    assert abs(e["E2"] - g["E2"]) <= ENERGY_TOL, (e["E2"], g["E2"])
+    assert abs(e["E3"] - g["E3"]) <= ENERGY_TOL, (e["E3"], g["E3"])
+
+
 @pytest.mark.parametrize("t,U", [(1.0, 4.0), (1.0, 1.0)])
 def test_dimer_lcc_closed_form(mpslcc, t, U):
     """E0 = -2t + U/2, E2 = -U^2/(16t), E3 = 0 for the bonding/antibonding
