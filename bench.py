@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import pickle
 import os
 import subprocess
 import sys
@@ -47,8 +48,14 @@ def parse():
                     help="reference start: lowest-h_pp determinant or random MPS")
     ap.add_argument("--prec", default="bf16x3", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64-sweep", action="store_true",
-                    help="skip the FP64 comparison sweep (same states, plain FP64 path)")
+    ap.add_argument("--save-state", default=None,
+                    help="after the timed steps, write the reference and first-order MPS to this file")
+    ap.add_argument("--load-state", default=None,
+                    help="start from states written by --save-state instead of the reference sweeps "
+                         "(used to profile the timed sweep without the set-up)")
+    ap.add_argument("--fp64-sweep", action="store_true",
+                    help="also time one sweep on the plain FP64 path from the same states (about 8 minutes "
+                         "at M1 = 2000)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="profiling mode: N sigma products at the middle position inside NVTX range 'sigma'")
@@ -266,7 +273,14 @@ def gpu_arm(args, rank, world, local_rank):
                      init_guess=1 if args.dmrg_init == "product" else 0)
     ctx.build_mpo(c["h"], c["V"], c["n_alpha"] + c["n_beta"], 0)
     ctx.set_spaces(c["n_core"], c["n_active"])
-    E0 = ctx.dmrg_reference(M0, args.dmrg_sweeps)
+    if args.load_state:
+        with open(args.load_state, "rb") as f:
+            saved = pickle.load(f)
+        ctx.load_mps(0, saved["phi0"])
+        E0 = ctx.dmrg_reference(M0, 0)
+        ctx.load_mps(1, saved["phi1"])
+    else:
+        E0 = ctx.dmrg_reference(M0, args.dmrg_sweeps)
     for _ in range(args.warmup):
         ctx.lcc_sweep(M1, 1)
     stream = torch.cuda.current_stream()
@@ -352,6 +366,7 @@ def gpu_arm(args, rank, world, local_rank):
                         "l2": "working set (environments, fused operators) far above L2"},
                 sweep_s=dev_s / args.steps, sigma_calls=st["sigma_calls"], sigma_kernel_s=kern,
                 stage_s={k: st[k] for k in ("t_plan", "t_rhs", "t_solve", "t_trunc", "t_env", "t_fuse_left", "t_fuse_right", "t_tc_prepare")},
+                fused_ahead={"used": st["ahead_used"], "missed": st["ahead_missed"]},
                 energies={k: e[k] for k in ("E0", "E2", "E3", "E_lcc2", "E_lcc3", "max_discarded_weight")},
                 roofline=roof, gpu_launches=st["kernel_launches"],
                 e2e={"value": world * flops2 / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
@@ -359,7 +374,10 @@ def gpu_arm(args, rank, world, local_rank):
     clk_s = clk.summary()
     if clk_s:
         line["clocks"] = clk_s
-    if not args.no_fp64_sweep and prec != 0:
+    if args.save_state:
+        with open(args.save_state, "wb") as f:
+            pickle.dump({"phi0": ctx.export_mps(0), "phi1": ctx.export_mps(1)}, f, protocol=4)
+    if args.fp64_sweep and prec != 0:
         # the same sweep on the plain FP64 path (DFMA GEMMs), from the same
         # reference and first-order states, outside the timed region
         p0, p1 = ctx.export_mps(0), ctx.export_mps(1)

@@ -143,6 +143,9 @@ typedef struct {
   double t_fuse_left;       /* wall seconds building L' (all sweeps)         */
   double t_fuse_right;      /* ... building R'                               */
   double t_tc_prepare;      /* ... low-precision copies of L', R' and tasks  */
+  long long ahead_used;     /* fused operators built during the previous
+                               truncation and used by the next plan          */
+  long long ahead_missed;   /* ... discarded (middle sectors had changed)    */
 } mpslcc_stats;
 
 /* Fill *opts with defaults (device 0, FP64, tol 1e-10, max_iter 200, auto

@@ -60,7 +60,8 @@ class Stats(C.Structure):
                 ("f64_phase1_seconds", C.c_double), ("f64_phase2_seconds", C.c_double),
                 ("tc_launches", C.c_longlong), ("t_plan", C.c_double), ("t_trunc", C.c_double),
                 ("t_env", C.c_double), ("t_solve", C.c_double), ("t_rhs", C.c_double),
-                ("t_fuse_left", C.c_double), ("t_fuse_right", C.c_double), ("t_tc_prepare", C.c_double)]
+                ("t_fuse_left", C.c_double), ("t_fuse_right", C.c_double), ("t_tc_prepare", C.c_double),
+                ("ahead_used", C.c_longlong), ("ahead_missed", C.c_longlong)]
 
 
 def _load():

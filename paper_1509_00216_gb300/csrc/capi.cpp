@@ -540,6 +540,8 @@ mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out) {
     out->t_fuse_left = c.st.t_fuse_left;
     out->t_fuse_right = c.st.t_fuse_right;
     out->t_tc_prepare = c.st.t_tc_prepare;
+    out->ahead_used = c.st.ahead_used;
+    out->ahead_missed = c.st.ahead_missed;
     out->t_solve = c.st.t_solve;
     out->t_rhs = c.st.t_rhs;
   });

@@ -674,14 +674,13 @@ void two_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long
 }
 
 void build_fused_ahead(Ctx& c, Family& F, int l, bool right_side, FusedAhead& A) {
-  std::vector<QN> mb, mk;
   std::vector<long> ob, ok;
   long nb = 0, nk = 0;
-  two_site_middle(*F.bra, l, mb, ob, nb);
-  two_site_middle(*F.ket, l, mk, ok, nk);
   A.l = -1;
-  if (right_side) make_right_fused(c, F, l + 1, mb, mk, A.rf);
-  else make_left_fused(c, F, l, mb, mk, A.lf);
+  two_site_middle(*F.bra, l, A.mid_b, ob, nb);
+  two_site_middle(*F.ket, l, A.mid_k, ok, nk);
+  if (right_side) make_right_fused(c, F, l + 1, A.mid_b, A.mid_k, A.rf);
+  else make_left_fused(c, F, l, A.mid_b, A.mid_k, A.lf);
   A.l = l;
   A.right = right_side;
 }
@@ -692,8 +691,10 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead) 
   P.fam = &F;
   two_site_middle(*F.bra, l, P.mid_b, P.off_b, P.nb);
   two_site_middle(*F.ket, l, P.mid_k, P.off_k, P.nk);
-  const bool have_l = ahead && ahead->l == l && !ahead->right;
-  const bool have_r = ahead && ahead->l == l && ahead->right;
+  const bool match = ahead && ahead->l == l && ahead->mid_b == P.mid_b && ahead->mid_k == P.mid_k;
+  const bool have_l = match && !ahead->right;
+  const bool have_r = match && ahead->right;
+  if (ahead && ahead->l == l) (match ? c.st.ahead_used : c.st.ahead_missed)++;
   if (have_l) {
     P.lf = std::move(ahead->lf);
   } else {

@@ -146,10 +146,13 @@ struct RightFused {
 // (while the truncation at the neighbouring position runs): the right side
 // R' of site l+1 during a left-to-right sweep, the left side L' of site l
 // during a right-to-left sweep.  Neither depends on the sites that
-// truncation changes.
+// truncation changes, but both are keyed by the middle sectors of position
+// l, which can change with the truncated bond: the plan uses it only when
+// they did not.
 struct FusedAhead {
   int l = -1;
-  bool right = false;  // holds rf (else lf)
+  bool right = false;              // holds rf (else lf)
+  std::vector<QN> mid_b, mid_k;    // middle sectors it was built for
   LeftFused lf;
   RightFused rf;
 };
@@ -195,6 +198,7 @@ struct Stats {
   // host wall time per sweep stage (stream-synchronised)
   double t_plan = 0, t_trunc = 0, t_env = 0, t_solve = 0, t_rhs = 0;
   double t_fuse_left = 0, t_fuse_right = 0, t_tc_prepare = 0;
+  long long ahead_used = 0, ahead_missed = 0;
 };
 
 // Adds the wall time of a scope (after synchronising the stream) to *acc.

@@ -206,8 +206,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ int find_tc(const TcTask* t, int n, long long tile) {
-  int lo = 0, hi = n - 1;
+// A CTA visits its tiles in increasing order, so the owning task index never
+// decreases: step forward from the previous one (usually zero or one step),
+// with a binary search for long jumps.
+__device__ __forceinline__ int next_tc(const TcTask* t, int n, long long tile, int prev) {
+  int i = prev;
+  for (int s = 0; s < 4; ++s) {
+    if (i + 1 >= n || t[i + 1].tile0 > tile) return i;
+    ++i;
+  }
+  int lo = i, hi = n - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     if (t[mid].tile0 <= tile) lo = mid;
@@ -264,17 +272,30 @@ __device__ __forceinline__ void store_row(const TcTask* T, long long roff, int c
         pm[j] = *reinterpret_cast<const uint32_t*>(&m);
         pl[j] = *reinterpret_cast<const uint32_t*>(&l);
       }
-      const uint32_t* blk[6] = {ph, pm, pm, ph, pl, ph};
+      // block order [h m m h l h]
+      uint4* d0 = reinterpret_cast<uint4*>(C);
+      uint4* d1 = reinterpret_cast<uint4*>(C + T->soff);
+      uint4* d2 = reinterpret_cast<uint4*>(C + 2 * T->soff);
+      uint4* d3 = reinterpret_cast<uint4*>(C + 3 * T->soff);
+      uint4* d4 = reinterpret_cast<uint4*>(C + 4 * T->soff);
+      uint4* d5 = reinterpret_cast<uint4*>(C + 5 * T->soff);
 #pragma unroll
-      for (int b = 0; b < 6; ++b) {
-        uint4* d = reinterpret_cast<uint4*>(C + b * T->soff);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          d[q] = make_uint4(blk[b][4 * q], blk[b][4 * q + 1], blk[b][4 * q + 2], blk[b][4 * q + 3]);
+      for (int q = 0; q < 4; ++q) {
+        const uint4 h4 = make_uint4(ph[4 * q], ph[4 * q + 1], ph[4 * q + 2], ph[4 * q + 3]);
+        const uint4 m4 = make_uint4(pm[4 * q], pm[4 * q + 1], pm[4 * q + 2], pm[4 * q + 3]);
+        const uint4 l4 = make_uint4(pl[4 * q], pl[4 * q + 1], pl[4 * q + 2], pl[4 * q + 3]);
+        d0[q] = h4;
+        d1[q] = m4;
+        d2[q] = m4;
+        d3[q] = h4;
+        d4[q] = l4;
+        d5[q] = h4;
       }
       return;
     }
-    for (int j = 0; j < nv; ++j) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= nv) break;
       const float f = __uint_as_float(v[j]);
       const __nv_bfloat16 h = __float2bfloat16_rn(f);
       const float r = f - __bfloat162float(h);
@@ -297,24 +318,47 @@ __device__ __forceinline__ void store_row(const TcTask* T, long long roff, int c
                          __uint_as_float(v[4 * q + 3]));
     return;
   }
+  // the remaining paths index v only with unrolled constants, so that the
+  // accumulator row stays in registers
   if (T->mode == 4) {
     double* C = (double*)T->C + roff + c0;
-    if (T->beta == 0.0)
-      for (int j = 0; j < nv; ++j) C[j] = T->alpha * (double)__uint_as_float(v[j]);
-    else
-      for (int j = 0; j < nv; ++j) C[j] = T->alpha * (double)__uint_as_float(v[j]) + T->beta * C[j];
+    const double al = T->alpha, be = T->beta;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= nv) break;
+      const double x = al * (double)__uint_as_float(v[j]);
+      C[j] = be == 0.0 ? x : x + be * C[j];
+    }
     return;
   }
   if (T->mode == 0) {
     float* C = (float*)T->C + roff + c0;
-    for (int j = 0; j < nv; ++j) atomicAdd(C + j, __uint_as_float(v[j]));
+    if (nv == 32 && ((uintptr_t)C & 15) == 0) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        atomicAdd(reinterpret_cast<float4*>(C) + q,
+                  make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]), __uint_as_float(v[4 * q + 2]),
+                              __uint_as_float(v[4 * q + 3])));
+      return;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= nv) break;
+      atomicAdd(C + j, __uint_as_float(v[j]));
+    }
   } else if (T->mode == 1) {
     __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
-    for (int j = 0; j < nv; ++j) C[j] = __float2bfloat16_rn(__uint_as_float(v[j]));
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= nv) break;
+      C[j] = __float2bfloat16_rn(__uint_as_float(v[j]));
+    }
   } else if (T->mode == 3) {
     // two-term BF16 split of the FP32 result: [hi | lo]
     __nv_bfloat16* C = (__nv_bfloat16*)T->C + roff + c0;
-    for (int j = 0; j < nv; ++j) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= nv) break;
       const float f = __uint_as_float(v[j]);
       const __nv_bfloat16 h = __float2bfloat16_rn(f);
       const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
@@ -323,7 +367,11 @@ __device__ __forceinline__ void store_row(const TcTask* T, long long roff, int c
     }
   } else {
     float* C = (float*)T->C + roff + c0;
-    for (int j = 0; j < nv; ++j) C[j] = __uint_as_float(v[j]);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= nv) break;
+      C[j] = __uint_as_float(v[j]);
+    }
   }
 }
 
@@ -374,8 +422,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
       uint32_t it = 0;
+      int ti = 0;
       for (long long tile = blockIdx.x; tile < total && !*s_abort; tile += gridDim.x) {
-        const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
+        ti = next_tc(tasks, ntasks, tile, ti);
+        const TcTask* T = &tasks[ti];
         const TileCoord tc = tile_coord(T, tile);
         const int kt0 = tc.ks * T->kchunk;
         const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
@@ -399,8 +449,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       uint32_t it = 0, tcount = 0;
+      int ti = 0;
       for (long long tile = blockIdx.x; tile < total && !*s_abort; tile += gridDim.x, ++tcount) {
-        const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
+        ti = next_tc(tasks, ntasks, tile, ti);
+        const TcTask* T = &tasks[ti];
         const TileCoord tc = tile_coord(T, tile);
         const int kt0 = tc.ks * T->kchunk;
         const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
@@ -437,8 +489,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
     // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31
     const int quarter = warp & 3;
     uint32_t tcount = 0;
+    int ti = 0;
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
-      const TcTask* T = &tasks[find_tc(tasks, ntasks, tile)];
+      ti = next_tc(tasks, ntasks, tile, ti);
+      const TcTask* T = &tasks[ti];
       const TileCoord tc = tile_coord(T, tile);
       const int row0 = tc.tmi * 128, col0 = tc.tni * T->ntile;
       const int ntile = T->ntile;
