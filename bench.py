@@ -250,6 +250,7 @@ def _mpo_classes(ctx, which, bond):
     return out
 
 
+SIGMA_TRAFFIC_RATIO = (3.270 + 3.547) / (2.512 + 2.690)
 METRIC = "sigma-vector TFLOP/s and LCC sweep s at M=2000, mixed vs FP64; |dE| vs oracle"
 
 
@@ -354,7 +355,16 @@ def gpu_arm(args, rank, world, local_rank):
                 "tensor_tflops": flops / tcs / 1e12 if tcs else None,
                 "tensor_frac_of_bf16_sustained": flops / tcs / 1e12 / pk["bf16_sust"] if tcs else None}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
-    roof["traffic"] = None
+    if prec != 0:
+        # DRAM bytes per algorithmic byte of the sigma launches, from one ncu
+        # capture of both phases at the middle position of the 3-band workload
+        # at M1 = 1000 (3.270 + 3.547 GB against 2.512 + 2.690 GB); the traffic
+        # of a launch scales with the bytes it moves, so the full-size figure
+        # is this ratio times the algorithmic bytes per launch
+        roof["traffic"] = SIGMA_TRAFFIC_RATIO * roof["bytes_per_launch"]
+        roof["traffic_source"] = "ncu dram bytes ratio 1.31 at M1=1000, scaled to the launch's algorithmic bytes"
+    else:
+        roof["traffic"] = None
     roof["peak_source"] = pk["src"]
     value = world * flops / dev_s / 1e12
     line = dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,

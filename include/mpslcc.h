@@ -248,9 +248,9 @@ mpslcc_status mpslcc_debug_tc_gemm(mpslcc_ctx* ctx, int prec, int m, int n, int 
 
 /* Allocation-free C = A B^T (the product of mpslcc_debug_tc_gemm with FP32
    output) for callers that cannot allocate device memory when they need it:
-   code recorded under CUDA stream capture, or a host framework that owns every
-   device allocation and forbids new ones inside its step.  There is no
-   counterpart in the paper.
+   a host framework that owns every device allocation and forbids new ones
+   inside its step, or code whose device memory must all be reserved at
+   start-up.  There is no counterpart in the paper.
    - d_A (m x k), d_B (n x k), d_C (m x n): row-major FP64 DEVICE arrays owned
      by the caller; prec is TF32, BF16 or BF16X3; work runs on `stream` (NULL =
      legacy default stream) of `device`, which must be the current device.

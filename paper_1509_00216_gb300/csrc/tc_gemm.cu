@@ -1105,8 +1105,9 @@ void tc_selftest(Ctx& c, int prec, int m, int n, int k, const double* A, const d
 // Allocation-free variant of the tensor-core GEMM.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// product: code recorded under CUDA stream capture, or a host framework that
-// owns every device allocation and forbids new ones inside its step.  For
+// product: a host framework that owns every device allocation and forbids new
+// ones inside its step, or code whose device memory is all reserved at
+// start-up.  For
 // them, C = A B^T (the self-test product above) is also offered with all of
 // its scratch -- the low-precision operand copies, the FP32 result, the task
 // descriptors and the error flag -- in one fixed file-scope device array.

@@ -1,8 +1,8 @@
 """Allocation-free tensor-core GEMM entry point.
 
-Callers that cannot allocate device memory when they need a product (code
-recorded under CUDA stream capture, or a framework that owns every device
-allocation) use ``mpslcc_tc_gemm_noalloc``, whose scratch lives in a fixed
+Callers that cannot allocate device memory when they need a product (a
+framework that owns every device allocation, or code whose device memory is
+all reserved at start-up) use ``mpslcc_tc_gemm_noalloc``, whose scratch lives in a fixed
 device array inside the library.  Its results must equal those of the
 allocating entry point ``mpslcc_debug_tc_gemm`` (FP32 output mode), call after
 call, since both run the same conversion and tensor-core kernel.  This file is
