@@ -110,3 +110,46 @@ def test_build_mpo_rejects_bad_input(mpslcc):
         ctx.set_spaces(1, 1)  # before build_mpo
     assert e.value.status == 2
     ctx.close()
+
+
+def _header_structs(hdr):
+    """Field names, in order, of every `typedef struct { ... } name;` in the header."""
+    text = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        fields = []
+        for stmt in body.split(";"):
+            stmt = stmt.strip()
+            if not stmt:
+                continue
+            fp = re.search(r"\(\s*\*\s*(\w+)\s*\)", stmt)
+            fields.append(fp.group(1) if fp else re.findall(r"\w+", stmt)[-1])
+        out[name] = fields
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("mpslcc_opts", "Opts"), ("mpslcc_energies", "Energies"),
+                                          ("mpslcc_stats", "Stats")])
+def test_binding_structs_match_header_layout(mpslcc, cname, pyname, tmp_path):
+    """The ctypes mirrors of the ABI structs have the header's fields, in order,
+    at the offsets a C compiler gives them."""
+    import shutil
+    import subprocess
+    hdr = open(os.path.join(ROOT, "include", "mpslcc.h")).read()
+    fields = _header_structs(hdr)[cname]
+    py = getattr(mpslcc, pyname)
+    assert [f[0] for f in py._fields_] == fields
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpslcc.h"', "int main(void) {",
+             f'  printf("%zu\\n", sizeof({cname}));']
+    lines += [f'  printf("%zu\\n", offsetof({cname}, {f}));' for f in fields]
+    lines += ["  return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I" + os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(py)
+    assert got[1:] == [getattr(py, f).offset for f in fields]
