@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <functional>
 #include <random>
 #include <thread>
@@ -433,25 +434,28 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     }
   };
   std::vector<std::thread> pool;
+  std::exception_ptr failed;
   if (overlap) {
     for (int sidx = 0; sidx < nthreads; ++sidx) pool.emplace_back(worker, sidx);
     try {
       overlap();
     } catch (...) {
-      for (auto& th : pool) th.join();
-      throw;
+      failed = std::current_exception();
     }
   } else {
     for (int sidx = 1; sidx < nthreads; ++sidx) pool.emplace_back(worker, sidx);
     worker(0);
   }
   for (auto& th : pool) th.join();
-  for (int sidx = 0; sidx < nthreads; ++sidx) MPSLCC_REQUIRE(!bad[sidx], ST_CUDA, "cusolverDnDsyevd failed");
-  c.st.kernel_launches += ns;
+  // the main stream waits for every side stream before anything is freed on
+  // it (the density matrices), on the error paths too
   for (int sidx = 0; sidx < Ctx::NEIG; ++sidx) {
     cuda_check(cudaEventRecord(c.eig_ev[sidx], c.eig_stream[sidx]), "eig join");
     cudaStreamWaitEvent(c.s(), c.eig_ev[sidx], 0);
   }
+  if (failed) std::rethrow_exception(failed);
+  for (int sidx = 0; sidx < nthreads; ++sidx) MPSLCC_REQUIRE(!bad[sidx], ST_CUDA, "cusolverDnDsyevd failed");
+  c.st.kernel_launches += ns;
   std::vector<double> hw(std::max(wtot, 1L));
   cuda_check(cudaMemcpyAsync(hw.data(), w.p, wtot * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "eig d2h");
   cuda_check(cudaStreamSynchronize(c.s()), "eig sync");
