@@ -178,3 +178,30 @@ def test_isometry_reproduces_mps_vector():
         psi[j] = tot
     P = omps.isometry(m, l, dets)
     np.testing.assert_allclose(P @ psi, full, atol=1e-12)
+
+
+def test_energy_formulas_hold_for_states_not_orthogonal_to_the_reference():
+    """The energies are evaluated from overlaps of an MPS Phi1 that need not be
+    exactly orthogonal to Phi0.  With s = <1|0> and Q Phi1 = Phi1 - s Phi0:
+      J(Q Phi1)  = <1|H0|1> - E0 <1|1> - 2 s (<1|H0|0> - E0 s) + 2 (<1|H|0> - s E0),
+      E3(Q Phi1) = <1|U|1> - 2 s (<1|H|0> - <1|H0|0>)      (<0|U|0> = 0).
+    Checked against the definitions applied to Q Phi1 for the exact first-order
+    state plus a reference admixture and plus a random perturbation."""
+    c = synth.config(0)
+    r = lcc.lcc_energies(c["h"], c["V"], 4, 4, c["n_core"], c["n_active"])
+    H, H0, phi0, E0, x, b = (r["H"].toarray(), r["H0"].toarray(), r["phi0"], r["E0"], r["x"], r["b"])
+    U = H - H0
+    assert abs(phi0 @ U @ phi0) < 1e-12
+    rng = np.random.default_rng(5)
+    A = H0 - E0 * np.eye(len(phi0))
+    for phi1 in (x + 0.3 * phi0, x + 0.01 * rng.standard_normal(len(x))):
+        s = phi1 @ phi0
+        q = phi1 - s * phi0
+        J_def = q @ A @ q - 2.0 * (q @ b)
+        E3_def = q @ U @ q
+        J_form = (phi1 @ H0 @ phi1 - E0 * (phi1 @ phi1) - 2 * s * (phi1 @ H0 @ phi0 - E0 * s)
+                  + 2 * (phi1 @ H @ phi0 - s * E0))
+        E3_form = phi1 @ U @ phi1 - 2 * s * (phi1 @ H @ phi0 - phi1 @ H0 @ phi0)
+        assert abs(J_form - J_def) < 1e-11
+        assert abs(E3_form - E3_def) < 1e-11
+    assert abs(r["J"] - r["E2"]) < 1e-12
