@@ -25,6 +25,7 @@ import pickle
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -81,7 +82,9 @@ class Clocks:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # samples go to $MPSLCC_CLOCKS_DIR (default: the system temp directory)
+        self.out = os.path.join(os.environ.get("MPSLCC_CLOCKS_DIR", tempfile.gettempdir()),
+                                f"mpslcc_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
