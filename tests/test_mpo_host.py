@@ -112,6 +112,26 @@ def test_build_mpo_rejects_bad_input(mpslcc):
     ctx.close()
 
 
+def test_host_only_context_contract(mpslcc):
+    """Option checks run at creation; a host-only context (device = -1) builds
+    and exports MPOs but refuses every call that runs kernels, with E_STATE and
+    a message, and stays usable afterwards."""
+    for kw in ({"prec": 7}, {"init_guess": 3}):
+        with pytest.raises(mpslcc.MpsLccError) as e:
+            mpslcc.Context(device=-1, **kw)
+        assert e.value.status == 1
+    h, V = _integrals(4, 2)
+    ctx = mpslcc.Context(device=-1)
+    ctx.build_mpo(h, V, n_elec=4, two_sz=0)
+    ctx.set_spaces(1, 2)
+    for call in (lambda: ctx.dmrg_reference(8, 1), lambda: ctx.lcc_sweep(8, 1), lambda: ctx.energy()):
+        with pytest.raises(mpslcc.MpsLccError) as e:
+            call()
+        assert e.value.status == 2 and str(e.value)
+    assert len(ctx.mpo_bond_dims(mpslcc.MPO_H0)) == 5
+    ctx.close()
+
+
 def _header_structs(hdr):
     """Field names, in order, of every `typedef struct { ... } name;` in the header."""
     text = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
