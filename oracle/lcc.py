@@ -74,6 +74,32 @@ def first_order(H, H0, phi0, E0, dets, n_orb, n_core, n_active):
     return dict(x=x, b=b, E2=E2, E3=E3, J=J, norm2=x @ x)
 
 
+def state_energies(H, H0, phi0, phi1):
+    """Energies of GIVEN states, as the definitions state them (Eq. 1b read
+    consistently with Eq. 1, and Eq. 2 with n = 1), for a reference phi0 and a
+    first-order vector phi1 that need not be optimal nor orthogonal to phi0
+    (an MPS of finite bond dimension is neither):
+      E0 = <phi0|H|phi0> / <phi0|phi0>,
+      q  = Q phi1 with Q = 1 - |phi0><phi0| (phi0 normalised),
+      b  = -Q H phi0,
+      J  = <q|(H0 - E0)|q> - 2 <q|b>          (Hylleraas value of q),
+      E3 = <q|H - H0|q>,
+      s  = <phi1|phi0>, norm1 = <phi1|phi1>.
+    """
+    Hd = _dense(H)
+    H0d = _dense(H0)
+    f = np.asarray(phi0, dtype=float)
+    f = f / np.linalg.norm(f)
+    E0 = f @ (Hd @ f)
+    s = float(np.asarray(phi1) @ f)
+    q = np.asarray(phi1, dtype=float) - s * f
+    b = -(Hd @ f)
+    b = b - f * (f @ b)
+    J = q @ (H0d @ q) - E0 * (q @ q) - 2.0 * (q @ b)
+    E3 = q @ ((Hd - H0d) @ q)
+    return dict(E0=E0, J=J, E2=J, E3=E3, overlap01=s, norm1=float(np.asarray(phi1) @ np.asarray(phi1)))
+
+
 def lcc_energies(h, V, n_alpha, n_beta, n_core, n_active):
     """E0 (CAS-CI reference), E2, E3 and FCI for a small Hamiltonian."""
     k = h.shape[0]

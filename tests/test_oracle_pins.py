@@ -205,3 +205,52 @@ def test_energy_formulas_hold_for_states_not_orthogonal_to_the_reference():
         assert abs(J_form - J_def) < 1e-11
         assert abs(E3_form - E3_def) < 1e-11
     assert abs(r["J"] - r["E2"]) < 1e-12
+
+
+def test_first_order_e3_equals_direct_third_order_energy():
+    """E3 of the first-order solve (Eq. 2, n = 1: <Phi1|U|Phi1>) equals the
+    third-order energy computed the other way, <Phi0|U|Phi(2)>, from the
+    second-order wavefunction of the Eq. 1 recursion; E2 likewise equals
+    <Phi0|U|Phi(1)> and the Wigner E(2), E(3).  A dropped term, sign or factor
+    in first_order's E3 changes one side only."""
+    c = synth.config(0)
+    k = 8
+    dets = fci.determinants(k, 4, 4)
+    H = fci.build_hamiltonian(c["h"], c["V"], dets)
+    H0 = fci.fink_h0(H, dets, k, c["n_core"], c["n_active"])
+    E0, phi0 = fci.cas_ci(H, dets, k, c["n_core"], c["n_active"])
+    r1 = lcc.first_order(H, H0, phi0, E0, dets, k, c["n_core"], c["n_active"])
+    rs = lcc.rspt(H, H0, phi0, 2, dets, k, c["n_core"], c["n_active"])
+    assert abs(r1["E2"] - rs["Edirect"][1]) < 1e-10
+    assert abs(r1["E3"] - rs["Edirect"][2]) < 1e-10, (r1["E3"], rs["Edirect"][2])
+    assert abs(r1["E3"] - rs["E"][3]) < 1e-10
+    assert abs(r1["E3"]) > 1e-3  # a non-trivial third-order energy
+
+
+def test_state_energies_at_the_solution_and_invariances():
+    """Energies of given states: at the exact first-order vector they are the
+    solve's E2 (= J) and E3; adding any multiple of Phi0 to Phi1 or rescaling
+    Phi0 changes nothing (Q projects the reference out); Phi1 = Phi0 gives
+    J = E3 = 0; and off the solution J exceeds E2 by exactly the quadratic
+    form <d|A|d> of the Q-space deviation d (A positive definite here)."""
+    c = synth.config(0)
+    r = lcc.lcc_energies(c["h"], c["V"], 4, 4, c["n_core"], c["n_active"])
+    H, H0, phi0, x = r["H"], r["H0"], r["phi0"], r["x"]
+    e = lcc.state_energies(H, H0, phi0, x)
+    assert abs(e["E0"] - r["E0"]) < 1e-12
+    assert abs(e["J"] - r["E2"]) < 1e-11 and abs(e["E3"] - r["E3"]) < 1e-11
+    assert abs(e["overlap01"]) < 1e-12
+    e2 = lcc.state_energies(H, H0, 2.0 * phi0, x - 0.7 * phi0)
+    assert abs(e2["J"] - e["J"]) < 1e-11 and abs(e2["E3"] - e["E3"]) < 1e-11
+    assert abs(e2["overlap01"] + 0.7) < 1e-12
+    e3 = lcc.state_energies(H, H0, phi0, phi0)
+    assert abs(e3["J"]) < 1e-12 and abs(e3["E3"]) < 1e-12
+    rng = np.random.default_rng(3)
+    Hd, H0d = H.toarray(), H0.toarray()
+    A = H0d - r["E0"] * np.eye(len(phi0))
+    for _ in range(3):
+        d = 1e-2 * rng.standard_normal(len(x))
+        d -= phi0 * (phi0 @ d)
+        ed = lcc.state_energies(H, H0, phi0, x + d)
+        assert ed["J"] > r["E2"]
+        assert abs((ed["J"] - r["E2"]) - d @ A @ d) < 1e-12
