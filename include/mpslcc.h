@@ -52,7 +52,9 @@ typedef enum {
   MPSLCC_E_NOMEM = 4,    /* device allocation failed                       */
   MPSLCC_E_NOCONV = 5,   /* iterative solver did not converge; result kept */
   MPSLCC_E_TIMEOUT = 6,  /* a bounded device wait gave up                  */
-  MPSLCC_E_INTERNAL = 7
+  MPSLCC_E_INTERNAL = 7,
+  MPSLCC_E_NUMERIC = 8   /* a non-finite value met inside an iterative
+                            solver (breakdown); see the sweep calls        */
 } mpslcc_status;
 
 /* FP64 DFMA; TF32 or BF16 tensor-core operands (FP32 accumulation); BF16X3:
@@ -99,6 +101,14 @@ typedef struct {
   int init_guess;        /* reference start: 0 = random MPS over all allowed
                             sectors (opts.seed), 1 = product state filling
                             the active orbitals of lowest h_pp            */
+  double wait_timeout_s; /* bound on every device-side wait of the tensor-core
+                            kernels, seconds (0 = 2 s, at most 60 s); a wait
+                            that runs out makes the call return
+                            MPSLCC_E_TIMEOUT and leaves the context usable  */
+  int tc_environments;   /* 1: the environments and fused operators that
+                            mpslcc_apply_heff builds run on the tensor cores
+                            as inside mixed-precision sweeps (three-piece
+                            BF16 split, about 2^-24 relative); 0: FP64     */
 } mpslcc_opts;
 
 typedef struct {
@@ -112,7 +122,23 @@ typedef struct {
   double norm1;     /* <Phi1|Phi1>                                           */
   double max_discarded_weight;
   int sweeps_done;
+  int flags;        /* MPSLCC_FLAG_* of the last sweep call and the energies */
 } mpslcc_energies;
+
+/* Bits of mpslcc_energies.flags. */
+enum {
+  MPSLCC_FLAG_NOCONV = 1,     /* a local solve stopped at max_iter above its
+                                 tolerance (the call returned E_NOCONV)      */
+  MPSLCC_FLAG_INDEFINITE = 2, /* a local LCC matrix Q(H0 - E0)Q showed a
+                                 non-positive curvature (MINRES was used): the
+                                 Hylleraas functional has no minimum there,
+                                 typically because Phi0 is not the lowest H0
+                                 state of the reference class                */
+  MPSLCC_FLAG_E2_POSITIVE = 4,/* E2 > 0: no Hylleraas minimum was reached     */
+  MPSLCC_FLAG_J_ROSE = 8      /* the local Hylleraas value rose from one
+                                 position to the next by more than 1e-6
+                                 relative (beyond truncation effects)        */
+};
 
 typedef struct {
   double sigma_flops;       /* algorithmic flops of all sigma products       */
@@ -146,6 +172,14 @@ typedef struct {
   long long ahead_used;     /* fused operators built during the previous
                                truncation and used by the next plan          */
   long long ahead_missed;   /* ... discarded (middle sectors had changed)    */
+  long long n_noconv;       /* local solves (Davidson, CG / MINRES) that
+                               stopped at max_iter above their tolerance    */
+  long long n_indefinite;   /* local LCC solves that met non-positive
+                               curvature and switched to MINRES             */
+  long long n_j_rise;       /* positions whose local Hylleraas value rose
+                               above the previous position's (1e-6 rel.)    */
+  double max_rel_residual;  /* largest final relative residual |b - Ax|/|b|
+                               of the local LCC solves of the last call      */
 } mpslcc_stats;
 
 /* Fill *opts with defaults (device 0, FP64, tol 1e-10, max_iter 200, auto
@@ -190,8 +224,11 @@ mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, doubl
    calls continue from the current Phi1. */
 mpslcc_status mpslcc_lcc_sweep(mpslcc_ctx* ctx, int M1, int order, int n_sweeps, double* E2_out);
 
-/* Eq. 2: energies of the current states (E3 = <Phi1|U|Phi1> is evaluated on
-   demand). */
+/* Eq. 1b and Eq. 2 (n = 1): energies of the current states, evaluated in
+   FP64 from the MPS tensors as they are (after sweeps, or as loaded with
+   mpslcc_load_mps): E0 of Phi0, and for Q Phi1 = Phi1 - <Phi0|Phi1> Phi0 the
+   Hylleraas value E2 = J(Q Phi1) and E3 = <Q Phi1|U|Q Phi1>.  Needs E0
+   (mpslcc_dmrg_reference); E2 / E3 are 0 while no Phi1 is present. */
 mpslcc_status mpslcc_energy(mpslcc_ctx* ctx, mpslcc_energies* out);
 
 /* Local dimension of the two-site vector at position site (0..n_orb-2) for

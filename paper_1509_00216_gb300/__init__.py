@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import warnings
 
 import numpy as np
 
@@ -21,7 +22,9 @@ OP_H0_11, OP_H0_00, OP_H_10, OP_U_11, OP_S_10, OP_H_11 = range(6)
 MPO_H, MPO_H0, MPO_U, MPO_ID = range(4)
 
 STATUS = {0: "OK", 1: "E_ARG", 2: "E_STATE", 3: "E_CUDA", 4: "E_NOMEM", 5: "E_NOCONV", 6: "E_TIMEOUT",
-          7: "E_INTERNAL"}
+          7: "E_INTERNAL", 8: "E_NUMERIC"}
+E_NOCONV = 5
+FLAG_NOCONV, FLAG_INDEFINITE, FLAG_E2_POSITIVE, FLAG_J_ROSE = 1, 2, 4, 8
 
 EXPORTED = [
     "mpslcc_default_opts", "mpslcc_create", "mpslcc_destroy", "mpslcc_last_error", "mpslcc_build_mpo",
@@ -40,13 +43,14 @@ class Opts(C.Structure):
                 ("max_iter", C.c_int), ("solver", C.c_int), ("davidson_max_subspace", C.c_int),
                 ("refine_steps", C.c_int), ("seed", C.c_ulonglong), ("verbose", C.c_int),
                 ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p),
-                ("init_guess", C.c_int)]
+                ("init_guess", C.c_int), ("wait_timeout_s", C.c_double), ("tc_environments", C.c_int)]
 
 
 class Energies(C.Structure):
     _fields_ = [("E0", C.c_double), ("E2", C.c_double), ("E3", C.c_double), ("E_lcc2", C.c_double),
                 ("E_lcc3", C.c_double), ("hylleraas", C.c_double), ("overlap01", C.c_double),
-                ("norm1", C.c_double), ("max_discarded_weight", C.c_double), ("sweeps_done", C.c_int)]
+                ("norm1", C.c_double), ("max_discarded_weight", C.c_double), ("sweeps_done", C.c_int),
+                ("flags", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -61,7 +65,8 @@ class Stats(C.Structure):
                 ("tc_launches", C.c_longlong), ("t_plan", C.c_double), ("t_trunc", C.c_double),
                 ("t_env", C.c_double), ("t_solve", C.c_double), ("t_rhs", C.c_double),
                 ("t_fuse_left", C.c_double), ("t_fuse_right", C.c_double), ("t_tc_prepare", C.c_double),
-                ("ahead_used", C.c_longlong), ("ahead_missed", C.c_longlong)]
+                ("ahead_used", C.c_longlong), ("ahead_missed", C.c_longlong), ("n_noconv", C.c_longlong),
+                ("n_indefinite", C.c_longlong), ("n_j_rise", C.c_longlong), ("max_rel_residual", C.c_double)]
 
 
 def _load():
@@ -118,6 +123,11 @@ class MpsLccError(RuntimeError):
         self.status = status
 
 
+class MpsLccNoConvergence(UserWarning):
+    """A sweep call returned MPSLCC_E_NOCONV: some local solves stopped at
+    max_iter above their tolerance; the call's states and energies were kept."""
+
+
 def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
@@ -141,7 +151,8 @@ class Context:
     allocator on the current torch stream."""
 
     def __init__(self, device=0, prec=FP64, tol=1e-10, max_iter=200, seed=7, verbose=0, refine_steps=4,
-                 davidson_max_subspace=24, torch_memory=False, init_guess=0):
+                 davidson_max_subspace=24, torch_memory=False, init_guess=0, wait_timeout_s=0.0, alloc=None,
+                 stream=None, tc_environments=False):
         L = lib()
         o = Opts()
         L.mpslcc_default_opts(C.byref(o))
@@ -154,8 +165,19 @@ class Context:
         o.refine_steps = refine_steps
         o.davidson_max_subspace = davidson_max_subspace
         o.init_guess = init_guess
+        o.wait_timeout_s = wait_timeout_s
+        o.tc_environments = 1 if tc_environments else 0
+        if stream is not None:
+            o.stream = C.c_void_p(stream)
         self._cb = None
-        if torch_memory and device >= 0:
+        self.last_status = 0
+        if alloc is not None:
+            # caller-provided (alloc(nbytes) -> int pointer or 0, free(ptr, nbytes)) pair
+            a_fn, f_fn = alloc
+            self._cb = (_ALLOC(lambda nbytes, user: a_fn(int(nbytes)) or None),
+                        _FREE(lambda ptr, nbytes, user: f_fn(ptr, int(nbytes))))
+            o.alloc, o.free = self._cb
+        elif torch_memory and device >= 0:
             import torch
             stream = torch.cuda.current_stream(device)
             o.stream = C.c_void_p(stream.cuda_stream)
@@ -192,7 +214,11 @@ class Context:
     def __exit__(self, *a):
         self.close()
 
-    def _check(self, st):
+    def _check(self, st, soft_noconv=False):
+        self.last_status = st
+        if st == E_NOCONV and soft_noconv:
+            warnings.warn(lib().mpslcc_last_error(self.h).decode(), MpsLccNoConvergence, stacklevel=3)
+            return
         if st != 0:
             raise MpsLccError(st, lib().mpslcc_last_error(self.h).decode())
 
@@ -209,12 +235,12 @@ class Context:
 
     def dmrg_reference(self, M0, n_sweeps):
         e = C.c_double()
-        self._check(lib().mpslcc_dmrg_reference(self.h, M0, n_sweeps, C.byref(e)))
+        self._check(lib().mpslcc_dmrg_reference(self.h, M0, n_sweeps, C.byref(e)), soft_noconv=True)
         return e.value
 
     def lcc_sweep(self, M1, n_sweeps, order=1):
         e = C.c_double()
-        self._check(lib().mpslcc_lcc_sweep(self.h, M1, order, n_sweeps, C.byref(e)))
+        self._check(lib().mpslcc_lcc_sweep(self.h, M1, order, n_sweeps, C.byref(e)), soft_noconv=True)
         return e.value
 
     def energy(self):

@@ -36,6 +36,20 @@ mpslcc_status guard(mpslcc_ctx* ctx, F&& f) {
 
 void need_device(Ctx& c) { MPSLCC_REQUIRE(!c.host_only, ST_STATE, "host-only context cannot run kernels"); }
 
+void require_finite(const double* x, size_t n, const char* what) {
+  for (size_t i = 0; i < n; ++i)
+    MPSLCC_REQUIRE(std::isfinite(x[i]), ST_ARG, std::string(what) + " contains a non-finite value");
+}
+
+// A sweep call whose local solves stopped at max_iter above their tolerance
+// still completes and keeps its results; it reports MPSLCC_E_NOCONV.
+mpslcc_status noconv_status(mpslcc_ctx* ctx, mpslcc_status st) {
+  if (st != MPSLCC_OK || ctx->c.cf.noconv == 0) return st;
+  ctx->c.err = std::to_string(ctx->c.cf.noconv) +
+               " local solve(s) stopped at max_iter above their tolerance; the states and energies were kept";
+  return MPSLCC_E_NOCONV;
+}
+
 void reset_families(Ctx& c) {
   for (Family* F : {&c.f00, &c.f11, &c.f10, &c.s10, &c.u11, &c.h11}) {
     F->L.clear();
@@ -143,10 +157,7 @@ mpslcc_status mpslcc_destroy(mpslcc_ctx* ctx) {
     for (DBuf* b : {&c.red, &c.red_out, &c.gtask, &c.ctask, &c.eig_work, &c.eig_w, &c.eig_info, &c.scratch_a,
                     &c.scratch_b, &c.scratch_tc, &c.tc_conv_tasks, &c.tc_gemm_tasks, &c.tc_err})
       b->release();
-    for (int s = 0; s < Ctx::NEIG; ++s) {
-      c.eig_ws[s].release();
-      c.eig_inf[s].release();
-    }
+    for (int s = 0; s < Ctx::NEIG; ++s) c.eig_ws[s].release();
     cudaStreamSynchronize(c.stream);
     for (int s = 0; s < Ctx::NEIG; ++s) {
       if (c.eig_solver[s]) cusolverDnDestroy(c.eig_solver[s]);
@@ -175,6 +186,8 @@ mpslcc_status mpslcc_build_mpo(mpslcc_ctx* ctx, const double* h, const double* V
                        std::abs(two_sz) <= 2 * n_orb - n_elec,
                    ST_ARG, "n_elec +- two_sz must be even and in range");
     int k = n_orb;
+    require_finite(h, (size_t)k * k, "h");
+    require_finite(V, (size_t)k * k * k * k, "V");
     for (int p = 0; p < k; ++p)
       for (int q = 0; q < k; ++q)
         MPSLCC_REQUIRE(std::fabs(h[p * k + q] - h[q * k + p]) <= 1e-10, ST_ARG, "h is not symmetric");
@@ -229,7 +242,8 @@ mpslcc_status mpslcc_set_spaces(mpslcc_ctx* ctx, int n_core, int n_active) {
 }
 
 mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, double* E0_out) {
-  return guard(ctx, [&](Ctx& c) {
+  if (ctx) ctx->c.cf.reset();
+  return noconv_status(ctx, guard(ctx, [&](Ctx& c) {
     need_device(c);
     MPSLCC_REQUIRE(c.have_mpo, ST_STATE, "build_mpo first");
     MPSLCC_REQUIRE(M0 >= 1 && n_sweeps >= 0, ST_ARG, "M0 must be positive and n_sweeps non-negative");
@@ -245,28 +259,31 @@ mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, doubl
       E = dmrg_reference(c, M0, n_sweeps);
     }
     if (E0_out) *E0_out = E;
-  });
+  }));
 }
 
 mpslcc_status mpslcc_lcc_sweep(mpslcc_ctx* ctx, int M1, int order, int n_sweeps, double* E2_out) {
-  return guard(ctx, [&](Ctx& c) {
+  if (ctx) ctx->c.cf.reset();
+  return noconv_status(ctx, guard(ctx, [&](Ctx& c) {
     need_device(c);
     MPSLCC_REQUIRE(order == 1, ST_ARG, "only first order (order = 1) is implemented");
     MPSLCC_REQUIRE(M1 >= 1 && n_sweeps >= 1, ST_ARG, "M1 and n_sweeps must be positive");
     cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
     double E2 = lcc_sweeps(c, M1, n_sweeps);
     if (E2_out) *E2_out = E2;
-  });
+  }));
 }
 
 mpslcc_status mpslcc_energy(mpslcc_ctx* ctx, mpslcc_energies* out) {
   return guard(ctx, [&](Ctx& c) {
     MPSLCC_REQUIRE(out, ST_ARG, "null output");
     MPSLCC_REQUIRE(c.have_E0, ST_STATE, "no reference energy yet");
-    if (c.have_E2 && !c.e_valid) {  // FP64 evaluation of the current state
+    if (c.phi1.present && c.phi0.present && !c.e_valid) {
+      // FP64 evaluation of the current states (optimised or loaded)
       need_device(c);
       cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
       compute_energies(c);
+      c.have_E2 = true;
     }
     std::memset(out, 0, sizeof(*out));
     out->E0 = c.E0;
@@ -279,6 +296,7 @@ mpslcc_status mpslcc_energy(mpslcc_ctx* ctx, mpslcc_energies* out) {
     out->norm1 = c.norm1;
     out->max_discarded_weight = c.max_disc;
     out->sweeps_done = c.sweeps_done;
+    out->flags = c.flags;
   });
 }
 
@@ -307,7 +325,15 @@ static void apply_heff_dev(Ctx& c, int site, int op, const double* d_psi, double
   MPSLCC_REQUIRE(prec >= MPSLCC_FP64 && prec <= MPSLCC_BF16X6, ST_ARG, "bad precision");
   Family& F = family_for(c, op);
   SigmaPlan P;
-  make_sigma_plan(c, F, site, P);
+  const int saved = c.gemm_prec;
+  c.gemm_prec = c.opts.tc_environments ? MPSLCC_BF16X3 : MPSLCC_FP64;
+  try {
+    make_sigma_plan(c, F, site, P);
+  } catch (...) {
+    c.gemm_prec = saved;
+    throw;
+  }
+  c.gemm_prec = saved;
   MPSLCC_REQUIRE(P.nk == n_in && P.nb == n_out, ST_ARG, "vector length does not match the local dimension");
   sigma_apply(c, P, d_psi, d_sigma, prec);
 }
@@ -316,6 +342,8 @@ mpslcc_status mpslcc_apply_heff(mpslcc_ctx* ctx, int site, int op, const double*
                                 long n_out, int prec) {
   return guard(ctx, [&](Ctx& c) {
     MPSLCC_REQUIRE(psi && sigma, ST_ARG, "null vector");
+    MPSLCC_REQUIRE(n_in >= 0 && n_out >= 0, ST_ARG, "negative vector length");
+    require_finite(psi, (size_t)n_in, "psi");
     need_device(c);
     cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
     DBuf x, y;
@@ -390,6 +418,7 @@ mpslcc_status mpslcc_load_mps(mpslcc_ctx* ctx, int which, int n_sites, const int
       MPSLCC_REQUIRE(!m.mask[p].empty(), ST_ARG, "site without blocks");
     }
     MPSLCC_REQUIRE(pos == n_data, ST_ARG, "n_data does not match the block sizes");
+    require_finite(data, (size_t)n_data, "MPS data");
     for (int p = 0; p < k; ++p) {
       long tot;
       std::vector<long> off = layout_offsets(m, p, 0, &tot);
@@ -418,7 +447,7 @@ mpslcc_status mpslcc_load_mps(mpslcc_ctx* ctx, int which, int n_sites, const int
     } else {
       c.phi1 = std::move(m);
     }
-    c.have_E2 = c.e3_valid = false;
+    c.have_E2 = c.e3_valid = c.e_valid = false;
   });
 }
 
@@ -544,6 +573,10 @@ mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out) {
     out->ahead_missed = c.st.ahead_missed;
     out->t_solve = c.st.t_solve;
     out->t_rhs = c.st.t_rhs;
+    out->n_noconv = c.st.n_noconv;
+    out->n_indefinite = c.st.n_indefinite;
+    out->n_j_rise = c.st.n_j_rise;
+    out->max_rel_residual = c.st.max_rel_residual;
   });
 }
 

@@ -37,7 +37,7 @@ struct Error : std::runtime_error {
   } while (0)
 
 enum { ST_OK = 0, ST_ARG = 1, ST_STATE = 2, ST_CUDA = 3, ST_NOMEM = 4, ST_NOCONV = 5,
-       ST_TIMEOUT = 6, ST_INTERNAL = 7 };
+       ST_TIMEOUT = 6, ST_INTERNAL = 7, ST_NUMERIC = 8 };
 
 // A list of sectors, sorted ascending by (N, 2Sz).
 struct Sectors {

@@ -140,7 +140,8 @@ void validate_gemm(const Ctx& c, const GemmTask& t) {
     c.check_range(t.A, 0, ea + (long long)(t.batch - 1) * t.sA, "gemm A");
     c.check_range(t.B, 0, eb + (long long)(t.batch - 1) * t.sB, "gemm B");
   }
-  c.check_range(t.C, 0, ec + (long long)(t.batch - 1) * t.sC, "gemm C");
+  const long long ek = (t.ksplit > 1 && t.sK > 0) ? (long long)(t.ksplit - 1) * t.sK : 0;
+  c.check_range(t.C, 0, ec + (long long)(t.batch - 1) * t.sC + ek, "gemm C");
   if ((!ta && t.lda < t.k) || (ta && t.lda < t.m) || (!tb && t.ldb < t.n) || (tb && t.ldb < t.k) || t.ldc < t.n)
     throw Error(ST_INTERNAL, "gemm leading dimension too small");
 }
@@ -720,8 +721,6 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead) 
   P.tt.alloc(&c, std::max(tts, 1L) * sizeof(double));
   P.xin.release();
   P.xin.alloc(&c, std::max(P.nk, 1L) * sizeof(double));
-  P.yout.release();
-  P.yout.alloc(&c, std::max(P.nb, 1L) * sizeof(double));
   std::vector<GemmTask> t1, t2;
   double fl = 0;
   for (const auto& S : rf.stk) {
@@ -739,25 +738,57 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead) 
     int dFLb = lf.FLb.d[lf.kb[bi]], dFRb = rf.FRb.d[rf.kb[bi]];
     base_tiles += (long long)((dFLb + 63) / 64) * ((dFRb + 63) / 64);
   }
+  // phase 2: one GEMM per middle sector with the channel sum in K, split over
+  // K when the sectors alone give too few tiles.  Every split stores its
+  // partial at its own offset of `ypart`; sigma_apply sums them in a fixed
+  // order (no atomics: results are reproducible bit for bit)
   const long long target = 152LL * 6;
-  P.zero_y = false;
+  std::vector<SplitSeg> segs;
+  std::vector<int> ksv(P.mid_b.size(), 0);
+  long poff = 0;
   for (size_t bi = 0; bi < P.mid_b.size(); ++bi) {
     long K = lf.K[bi];
     int dFLb = lf.FLb.d[lf.kb[bi]], dFRb = rf.FRb.d[rf.kb[bi]];
-    if (K == 0) {  // no operator channel reaches this output sector: it stays zero
-      P.zero_y = true;
-      continue;
+    SplitSeg sg;
+    std::memset(&sg, 0, sizeof(sg));
+    sg.out_off = P.off_b[bi];
+    sg.m = dFLb;
+    sg.n = dFRb;
+    sg.ldp = dFRb;
+    sg.sstride = (long long)dFLb * dFRb;
+    if (K > 0) {  // K = 0: no operator channel reaches this output sector, it stays zero
+      int ks = 1;
+      if (base_tiles < target) {
+        long long f = (target + base_tiles - 1) / std::max(1LL, base_tiles);
+        ks = (int)std::max(1LL, std::min(f, (long long)(K / 256)));
+      }
+      ksv[bi] = ks;
+      sg.nsplit = ks;
+      sg.part_off = poff;
+      poff += (long)ks * sg.sstride;
     }
-    GemmTask t = gemm(lf.data.d() + lf.off[bi], P.tt.d() + P.tt_off[bi], P.yout.d() + P.off_b[bi], dFLb, dFRb, (int)K,
-                      (int)K, (int)K, dFRb, GEMM_TB);
-    if (base_tiles < target) {
-      long long f = (target + base_tiles - 1) / std::max(1LL, base_tiles);
-      t.ksplit = (int)std::max(1LL, std::min(f, (long long)(K / 256)));
-      if (t.ksplit > 1) P.zero_y = true;
-    }
+    segs.push_back(sg);
+  }
+  P.ypart.release();
+  P.ypart.alloc(&c, std::max(poff, 1L) * sizeof(double));
+  for (size_t bi = 0; bi < P.mid_b.size(); ++bi) {
+    if (ksv[bi] == 0) continue;
+    long K = lf.K[bi];
+    int dFLb = lf.FLb.d[lf.kb[bi]], dFRb = rf.FRb.d[rf.kb[bi]];
+    GemmTask t = gemm(lf.data.d() + lf.off[bi], P.tt.d() + P.tt_off[bi], P.ypart.d() + segs[bi].part_off, dFLb, dFRb,
+                      (int)K, (int)K, (int)K, dFRb, GEMM_TB);
+    t.ksplit = ksv[bi];
+    t.sK = segs[bi].sstride;
     t2.push_back(t);
     fl += 2.0 * (double)dFLb * dFRb * K;
   }
+  P.nseg = (int)segs.size();
+  P.seg_tiles = plan_split_tiles(segs.data(), P.nseg);
+  P.segs.release();
+  P.segs.alloc(&c, std::max<size_t>(segs.size(), 1) * sizeof(SplitSeg));
+  if (!segs.empty())
+    cuda_check(cudaMemcpyAsync(P.segs.p, segs.data(), segs.size() * sizeof(SplitSeg), cudaMemcpyHostToDevice, c.s()),
+               "upload split segments");
   for (const auto& x : t1) validate_gemm(c, x);
   for (const auto& x : t2) validate_gemm(c, x);
   P.flops = fl;
@@ -785,17 +816,14 @@ void sigma_apply(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
   }
   if (P.nk > 0)
     cuda_check(cudaMemcpyAsync(P.xin.p, x, P.nk * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma in");
-  if (P.zero_y || P.n2 == 0)
-    cuda_check(cudaMemsetAsync(P.yout.p, 0, std::max(P.nb, 1L) * sizeof(double), c.s()), "sigma zero");
   cudaEventRecord(c.ev_p0, c.s());
   launch_gemm_f64((const GemmTask*)P.tasks1.p, P.n1, P.tiles1, c.s());
   cudaEventRecord(c.ev_p1, c.s());
   launch_gemm_f64((const GemmTask*)P.tasks2.p, P.n2, P.tiles2, c.s());
   cudaEventRecord(c.ev_p2, c.s());
+  launch_splitk_reduce_f64((const SplitSeg*)P.segs.p, P.nseg, P.seg_tiles, P.ypart.d(), y, c.s());
   cuda_check(cudaGetLastError(), "sigma launch");
-  if (P.nb > 0)
-    cuda_check(cudaMemcpyAsync(y, P.yout.p, P.nb * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma out");
-  c.st.kernel_launches += 2;
+  c.st.kernel_launches += 3;
   c.st.gemm_launches += 2;
   c.st.sigma_calls++;
   c.st.sigma_flops += P.flops;

@@ -168,11 +168,15 @@ struct SigmaPlan {
   long nb = 0, nk = 0;
   std::vector<long> tt_off;            // per bra middle
   DBuf tt;
-  DBuf xin, yout;
+  DBuf xin;
   DBuf tasks1, tasks2;
   int n1 = 0, n2 = 0;
   long long tiles1 = 0, tiles2 = 0;
-  bool zero_y = false;
+  // FP64 phase 2: per-split partial products and the segments of their
+  // fixed-order sum into sigma
+  DBuf ypart, segs;
+  int nseg = 0;
+  long long seg_tiles = 0;
   double flops = 0.0;                  // algorithmic flops of one application
   // low-precision operand copies and task lists of the tensor-core path:
   // tc for TF32 / BF16, tc6 for the three-piece layout (BF16X3 and BF16X6)
@@ -199,6 +203,15 @@ struct Stats {
   double t_plan = 0, t_trunc = 0, t_env = 0, t_solve = 0, t_rhs = 0;
   double t_fuse_left = 0, t_fuse_right = 0, t_tc_prepare = 0;
   long long ahead_used = 0, ahead_missed = 0;
+  long long n_noconv = 0, n_indefinite = 0, n_j_rise = 0;
+  double max_rel_residual = 0;
+};
+
+// Solver outcome counters of the current sweep call (reset per call).
+struct CallFlags {
+  long long noconv = 0, indefinite = 0, j_rise = 0;
+  double max_rel_residual = 0;
+  void reset() { *this = CallFlags(); }
 };
 
 // Adds the wall time of a scope (after synchronising the stream) to *acc.
@@ -238,6 +251,8 @@ struct Ctx {
   bool have_E0 = false, have_E2 = false, e3_valid = false, e_valid = false;
   int sweeps_done = 0;
   Stats st;
+  CallFlags cf;        // of the last dmrg_reference / lcc_sweep call
+  int flags = 0;       // MPSLCC_FLAG_* reported with the energies
 
   // families
   Family f00;   // <Phi0|H0|Phi0>
@@ -254,7 +269,7 @@ struct Ctx {
   cudaStream_t eig_stream[NEIG] = {};
   cusolverDnHandle_t eig_solver[NEIG] = {};
   cudaEvent_t eig_ev[NEIG] = {}, eig_fork = nullptr;
-  DBuf eig_ws[NEIG], eig_inf[NEIG];
+  DBuf eig_ws[NEIG];
   DBuf scratch_a, scratch_b;
   DBuf scratch_tc, tc_conv_tasks, tc_gemm_tasks, tc_err;
   // precision of the per-site FP64 GEMM tasks (fusion, renormalisation,

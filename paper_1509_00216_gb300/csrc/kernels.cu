@@ -95,10 +95,14 @@ __global__ void __launch_bounds__(GT) gemm_f64_kernel(const GemmTask* __restrict
       for (int j = 0; j < 4; ++j) {
         const int gj = col0 + tx + 16 * j;
         if (gj >= T.n) continue;
-        double* c = C + (long long)gi * T.ldc + gj;
         const double v = T.alpha * acc[i][j];
-        if (T.ksplit > 1) atomicAdd(c, v);
-        else *c = (T.beta != 0.0) ? v + T.beta * (*c) : v;
+        if (T.ksplit > 1 && T.sK > 0) {
+          C[(long long)ks * T.sK + (long long)gi * T.ldc + gj] = v;  // partial of split ks
+        } else {
+          double* c = C + (long long)gi * T.ldc + gj;
+          if (T.ksplit > 1) atomicAdd(c, v);
+          else *c = (T.beta != 0.0) ? v + T.beta * (*c) : v;
+        }
       }
     }
   }
@@ -120,6 +124,26 @@ __global__ void copy_f64_kernel(const CopyTask* __restrict__ tasks, int ntasks, 
       const double v = T.alpha * src[(long long)r * T.src_ld + c];
       double* d = dst + (long long)r * T.dst_ld + c;
       *d = T.accumulate ? *d + v : v;
+    }
+  }
+}
+
+constexpr int SPLIT_CHUNK = 4096;
+
+template <class T>
+__global__ void splitk_reduce_kernel(const SplitSeg* __restrict__ segs, int nseg, long long total,
+                                     const T* __restrict__ part, double* __restrict__ out) {
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const SplitSeg S = segs[find_task(segs, nseg, tile)];
+    const long long nel = (long long)S.m * S.n;
+    const long long e0 = (tile - S.tile0) * SPLIT_CHUNK;
+    const long long e1 = min(nel, e0 + SPLIT_CHUNK);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const int r = (int)(e / S.n), c = (int)(e - (long long)r * S.n);
+      const T* p = part + S.part_off + (long long)r * S.ldp + c;
+      double acc = 0.0;
+      for (int j = 0; j < S.nsplit; ++j) acc += (double)p[(long long)j * S.sstride];
+      out[S.out_off + e] = acc;
     }
   }
 }
@@ -259,6 +283,29 @@ long long plan_gemm_tiles(GemmTask* t, int n) {
     tot += (long long)t[i].batch * t[i].ksplit * t[i].tm * t[i].tn;
   }
   return tot;
+}
+
+long long plan_split_tiles(SplitSeg* s, int n) {
+  long long tot = 0;
+  for (int i = 0; i < n; ++i) {
+    s[i].tile0 = tot;
+    tot += ((long long)s[i].m * s[i].n + SPLIT_CHUNK - 1) / SPLIT_CHUNK;
+  }
+  return tot;
+}
+
+void launch_splitk_reduce_f32(const SplitSeg* d_segs, int nseg, long long total, const float* part, double* out,
+                              cudaStream_t s) {
+  if (total <= 0 || nseg <= 0) return;
+  int grid = (int)std::min<long long>(total, 152LL * 16);
+  splitk_reduce_kernel<float><<<grid, 256, 0, s>>>(d_segs, nseg, total, part, out);
+}
+
+void launch_splitk_reduce_f64(const SplitSeg* d_segs, int nseg, long long total, const double* part, double* out,
+                              cudaStream_t s) {
+  if (total <= 0 || nseg <= 0) return;
+  int grid = (int)std::min<long long>(total, 152LL * 16);
+  splitk_reduce_kernel<double><<<grid, 256, 0, s>>>(d_segs, nseg, total, part, out);
 }
 
 long long plan_copy_tiles(CopyTask* t, int n) {

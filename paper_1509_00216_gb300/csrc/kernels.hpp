@@ -8,9 +8,11 @@ namespace mpslcc {
 // One GEMM of a grouped launch: C = alpha * op(A) op(B) + beta * C for
 // `batch` problems at constant strides.  op(A) is m x k (A row-major m x k,
 // or k x m when transposed); op(B) is k x n (B row-major k x n, or n x k when
-// transposed).  With ksplit > 1 the K range is split across CTAs and partial
-// sums are added atomically (C must then be pre-scaled by the caller and
-// beta is ignored).
+// transposed).  With ksplit > 1 the K range is split across CTAs: with sK > 0
+// split j stores its partial product alpha * op(A) op(B)|_K-chunk j at C + j sK
+// (beta ignored; the partials are summed afterwards in a fixed order by
+// launch_splitk_reduce, so results do not depend on scheduling); with sK = 0
+// the partials are added to C atomically (C pre-scaled by the caller).
 struct GemmTask {
   const double* A;
   const double* B;
@@ -24,6 +26,7 @@ struct GemmTask {
   int ksplit;
   int tm, tn;     // tile counts (filled by plan_gemm_tiles)
   long long tile0;
+  long long sK;   // element stride between split-K partials (0 = atomic adds)
 };
 enum { GEMM_TA = 1, GEMM_TB = 2 };
 
@@ -62,6 +65,20 @@ void launch_lincomb(long n, int m, const double* V, long ld, const double* d_coe
 // proj[j] = <V_j, x> for j < m (batched dots), written to d_out[0..m)
 void launch_multidot(long n, int m, const double* V, long ld, const double* x, double* d_out,
                      double* d_partial, cudaStream_t s);
+
+// Fixed-order reduction of split-K partial products into an FP64 output
+// segment: out[out_off + r * n + c] = sum_{j < nsplit} part[part_off + j *
+// sstride + r * ldp + c] (summed in increasing j), or 0 when nsplit = 0.
+struct SplitSeg {
+  long long out_off, part_off, sstride;
+  int m, n, ldp, nsplit;
+  long long tile0;
+};
+long long plan_split_tiles(SplitSeg* s, int n);
+void launch_splitk_reduce_f32(const SplitSeg* d_segs, int nseg, long long total_tiles, const float* part,
+                              double* out, cudaStream_t s);
+void launch_splitk_reduce_f64(const SplitSeg* d_segs, int nseg, long long total_tiles, const double* part,
+                              double* out, cudaStream_t s);
 
 // Strided gather: dst[w*n + r] = src[off + w*sw + r*sr] per task (diagonals).
 struct GatherTask {

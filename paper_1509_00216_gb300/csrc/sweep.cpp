@@ -10,6 +10,7 @@
 #include <cstring>
 #include <exception>
 #include <functional>
+#include <memory>
 #include <random>
 #include <thread>
 
@@ -144,6 +145,8 @@ double davidson(Ctx& c, SigmaPlan& P, double* x, long n, const double* diag, dou
     lincomb(c, AV, n, m, y, r.d(), n);
     launch_axpy(n, -theta, xs.d(), r.d(), c.s());
     double rn = vnorm(c, r);
+    if (!std::isfinite(theta) || !std::isfinite(rn))
+      throw Error(ST_NUMERIC, "non-finite Ritz value or residual in the Davidson solve");
     if (rn < tol || n == 1 || m >= n) {
       *converged = true;
       break;
@@ -217,7 +220,8 @@ struct LinOp {
 // Preconditioned CG (MINRES when a non-positive curvature appears) for
 // A x = b, A = Q (H_eff - shift) Q.  Returns the final residual norm.
 double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* diag, long n, double tol, int maxit,
-                    int prec, int* iters, bool* indefinite) {
+                    int prec, int* iters, bool* indefinite, bool* hit_cap) {
+  *hit_cap = false;
   Vec r, z, p, Ap;
   r.alloc(c, n);
   z.alloc(c, n);
@@ -225,6 +229,7 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
   Ap.alloc(c, n);
   const double atol = 1e-14;
   double bn = std::sqrt(std::max(0.0, dev_dot(c, b, b, n)));
+  if (!std::isfinite(bn)) throw Error(ST_NUMERIC, "non-finite right-hand side in the local linear solve");
   if (bn <= atol) {  // right-hand side vanishes to working precision
     launch_fill(n, 0.0, x, c.s());
     *iters = 0;
@@ -249,8 +254,9 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
   while (rn > thr && it < maxit) {
     A.apply(c, p.d(), Ap.d(), prec);
     double pAp = dev_dot(c, p.d(), Ap.d(), n);
+    if (!std::isfinite(pAp)) throw Error(ST_NUMERIC, "non-finite curvature <p|A|p> in the local CG solve");
     if (!(pAp > 0)) {
-      *indefinite = std::isfinite(pAp);
+      *indefinite = true;
       break;
     }
     double alpha = rz / pAp;
@@ -261,6 +267,7 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
     launch_axpby(n, 1.0, z.d(), rz2 / rz, p.d(), c.s());
     rz = rz2;
     rn = vnorm(c, r);
+    if (!std::isfinite(rn)) throw Error(ST_NUMERIC, "non-finite residual in the local CG solve");
     ++it;
   }
   if (*indefinite) {
@@ -280,10 +287,12 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
     while (rn > thr && it < maxit && beta > 1e-300) {
       A.apply(c, v1.d(), av.d(), prec);
       double alpha = dev_dot(c, v1.d(), av.d(), n);
+      if (!std::isfinite(alpha)) throw Error(ST_NUMERIC, "non-finite Lanczos coefficient in the local MINRES solve");
       launch_axpy(n, -alpha, v1.d(), av.d(), c.s());
       launch_axpy(n, -beta, v0.d(), av.d(), c.s());
       betaold = beta;
       beta = vnorm(c, av);
+      if (!std::isfinite(beta)) throw Error(ST_NUMERIC, "non-finite Lanczos coefficient in the local MINRES solve");
       double d0 = gam1 * alpha - gam0 * sig1 * betaold;
       double r1 = std::sqrt(d0 * d0 + beta * beta);
       double r2 = sig1 * alpha + gam0 * gam1 * betaold;
@@ -313,8 +322,10 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
     copyv(c, r.d(), b, n);
     launch_axpy(n, -1.0, Ap.d(), r.d(), c.s());
     rn = vnorm(c, r);
+    if (!std::isfinite(rn)) throw Error(ST_NUMERIC, "non-finite residual in the local MINRES solve");
   }
   *iters = it;
+  *hit_cap = it >= maxit && rn > thr;
   return rn;
 }
 
@@ -402,10 +413,11 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     lwork = std::max(lwork, lw);
   }
   const int nthreads = std::max(1, std::min(Ctx::NEIG, ns));
-  for (int sidx = 0; sidx < nthreads; ++sidx) {
-    c.eig_ws[sidx].ensure(&c, (size_t)std::max(lwork, 1) * sizeof(double));
-    c.eig_inf[sidx].ensure(&c, sizeof(int) * 4);
-  }
+  for (int sidx = 0; sidx < nthreads; ++sidx) c.eig_ws[sidx].ensure(&c, (size_t)std::max(lwork, 1) * sizeof(double));
+  // one convergence flag (devInfo) per sector, read back after the join
+  DBuf info;
+  info.alloc(&c, (size_t)std::max(ns, 1) * sizeof(int));
+  cuda_check(cudaMemsetAsync(info.p, 0, (size_t)std::max(ns, 1) * sizeof(int), c.s()), "eig info zero");
   for (int i = 0; i < ns; ++i) {
     c.check_range(rho.d() + roff[i], 0, (long long)nd[i] * nd[i] - 1, "eigh matrix");
     c.check_range(w.d() + woff[i], 0, nd[i] - 1, "eigh values");
@@ -427,7 +439,7 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
       const int i = order[t];
       if (cusolverDnDsyevd(c.eig_solver[sidx], CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nd[i],
                            rho.d() + roff[i], nd[i], w.d() + woff[i], c.eig_ws[sidx].d(), lwork,
-                           (int*)c.eig_inf[sidx].p) != CUSOLVER_STATUS_SUCCESS) {
+                           (int*)info.p + i) != CUSOLVER_STATUS_SUCCESS) {
         bad[sidx] = 1;
         break;
       }
@@ -457,8 +469,16 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
   for (int sidx = 0; sidx < nthreads; ++sidx) MPSLCC_REQUIRE(!bad[sidx], ST_CUDA, "cusolverDnDsyevd failed");
   c.st.kernel_launches += ns;
   std::vector<double> hw(std::max(wtot, 1L));
+  std::vector<int> hinfo(std::max(ns, 1), 0);
   cuda_check(cudaMemcpyAsync(hw.data(), w.p, wtot * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "eig d2h");
+  cuda_check(cudaMemcpyAsync(hinfo.data(), info.p, ns * sizeof(int), cudaMemcpyDeviceToHost, c.s()), "eig info d2h");
   cuda_check(cudaStreamSynchronize(c.s()), "eig sync");
+  for (int i = 0; i < ns; ++i)
+    MPSLCC_REQUIRE(hinfo[i] == 0, ST_CUDA,
+                   "cusolverDnDsyevd did not converge for a density-matrix sector of dimension " +
+                       std::to_string(nd[i]) + " (info = " + std::to_string(hinfo[i]) + ")");
+  for (double v : hw)
+    MPSLCC_REQUIRE(std::isfinite(v), ST_NUMERIC, "non-finite density-matrix eigenvalue in the truncation");
   mark(2);
   // keep the M largest weights; ties by (sector, index)
   struct Ent { double v; int s, j; };
@@ -492,7 +512,6 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
       sidx.push_back(i);
     }
   MPSLCC_REQUIRE(nb.size() > 0, ST_INTERNAL, "truncation kept no states");
-  m.bond[l + 1] = nb;
   long isz = 0, csz = 0;
   for (size_t t = 0; t < sidx.size(); ++t) {
     int i = sidx[t];
@@ -533,6 +552,9 @@ double truncate(Ctx& c, MPS& m, int l, const double* psi, int M, bool moving_rig
     io += (long)nd[i] * kq;
   }
   run_gemm_tasks(c, ct);
+  // the new bond and both site tensors are committed together, after every
+  // step that can fail, so a failed truncation leaves the MPS as it was
+  m.bond[l + 1] = nb;
   if (moving_right) {
     set_site_lf(c, m, l, std::move(iso));
     set_site_rf(c, m, l + 1, std::move(cen));
@@ -744,6 +766,7 @@ void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed
 double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
   int k = c.k;
   const bool mixed = c.opts.prec != MPSLCC_FP64;
+  c.cf.reset();
   if (c.opts.init_guess == 1) init_product_mps(c, c.phi0);
   else init_random_mps(c, c.phi0, std::min(M0, 16), true, c.opts.seed);
   double E = 0;
@@ -767,6 +790,7 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
       double dtol = prec == MPSLCC_FP64 ? std::max(c.opts.tol, 1e-13) : std::max(c.opts.tol, 1e-4);
       E = davidson(c, P, x.d(), n, dg.d(), dtol, c.opts.max_iter, c.opts.davidson_max_subspace, &conv, prec);
       all_conv &= conv;
+      if (!conv) c.cf.noconv++;
       if (noise > 0)
         launch_noise(n, noise / std::sqrt((double)std::max(n, 1L)), tag * 1000003ull + (unsigned long long)l, x.d(),
                      c.s());
@@ -807,6 +831,8 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
   }
   c.E0 = E;
   c.have_E0 = true;
+  c.st.n_noconv += c.cf.noconv;
+  c.flags = c.cf.noconv ? MPSLCC_FLAG_NOCONV : 0;
   if (!all_conv && c.opts.verbose) fprintf(stderr, "[dmrg] warning: some Davidson solves hit max_iter\n");
   return E;
 }
@@ -822,7 +848,7 @@ double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, i
   long n = P11.nk, n0 = P10.nk;
   xb.alloc(&c, std::max(n, 1L) * sizeof(double));
   DBuf bb, ub, sb, dg, p0;
-  StageTimer* trhs = new StageTimer(c, &c.st.t_rhs);
+  std::unique_ptr<StageTimer> trhs(new StageTimer(c, &c.st.t_rhs));
   bb.alloc(&c, std::max(n, 1L) * sizeof(double));
   ub.alloc(&c, std::max(n, 1L) * sizeof(double));
   sb.alloc(&c, std::max(n, 1L) * sizeof(double));
@@ -843,16 +869,23 @@ double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, i
   project(c, u, bb.d(), n);
   form_two_site(c, c.phi1, l, xb.d());
   sigma_diag(c, P11, dg.d());
-  delete trhs;
-  StageTimer* tsol = new StageTimer(c, &c.st.t_solve);
+  trhs.reset();
+  std::unique_ptr<StageTimer> tsol(new StageTimer(c, &c.st.t_solve));
   LinOp A{&P11, c.E0, u, Vec()};
   int its = 0;
   bool indef = false;
   double bn = std::sqrt(std::max(0.0, dev_dot(c, bb.d(), bb.d(), n)));
+  if (!std::isfinite(bn)) throw Error(ST_NUMERIC, "non-finite right-hand side of the first-order equation");
   double J = 0;
+  bool cap = false;
+  auto note = [&](bool hit) {
+    if (hit) c.cf.noconv++;
+  };
   if (prec == MPSLCC_FP64) {
-    solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(c.opts.tol, 1e-14), c.opts.max_iter, prec, &its,
-                 &indef);
+    const double rfin = solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(c.opts.tol, 1e-14), c.opts.max_iter,
+                                     prec, &its, &indef, &cap);
+    note(cap);
+    if (bn > 0) c.cf.max_rel_residual = std::max(c.cf.max_rel_residual, rfin / bn);
     // local Hylleraas value J = x.Ax - 2 x.b (the FP64 value of the final
     // state comes from mpslcc_energy)
     Vec ax;
@@ -870,7 +903,10 @@ double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, i
     r.alloc(c, n);
     dx.alloc(c, n);
     ax.alloc(c, n);
-    solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(inner, c.opts.tol), c.opts.max_iter, prec, &its, &indef);
+    solve_linear(c, A, bb.d(), xb.d(), dg.d(), n, std::max(inner, c.opts.tol), c.opts.max_iter, prec, &its, &indef,
+                 &cap);
+    note(cap);
+    bool indef_any = indef;
     double rprev = HUGE_VAL;
     for (int ref = 0;; ++ref) {
       A.apply(c, xb.d(), ax.d(), MPSLCC_BF16X6);
@@ -880,8 +916,10 @@ double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, i
       // done at the target, once the residual stops falling (the floor of
       // the BF16X6 products, ~2^-24 |A| |x|), or after refine_steps
       // corrections; x.Ax = x.b - x.r gives the local Hylleraas value
+      if (!std::isfinite(rn)) throw Error(ST_NUMERIC, "non-finite refinement residual of the first-order equation");
       if (rn <= target || rn > 0.5 * rprev || ref >= c.opts.refine_steps) {
         J = -dev_dot(c, xb.d(), bb.d(), n) - dev_dot(c, xb.d(), r.d(), n);
+        if (bn > 0) c.cf.max_rel_residual = std::max(c.cf.max_rel_residual, rn / bn);
         break;
       }
       rprev = rn;
@@ -889,12 +927,16 @@ double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, i
       int it2 = 0;
       // the correction needs no more relative accuracy than the target asks
       const double itol = std::min(0.5, std::max(inner, target / rn));
-      solve_linear(c, A, r.d(), dx.d(), dg.d(), n, itol, c.opts.max_iter, prec, &it2, &indef);
+      solve_linear(c, A, r.d(), dx.d(), dg.d(), n, itol, c.opts.max_iter, prec, &it2, &indef, &cap);
+      note(cap);
+      indef_any |= indef;
       its += it2;
       launch_axpy(n, 1.0, dx.d(), xb.d(), c.s());
     }
+    indef = indef_any;
   }
-  delete tsol;
+  tsol.reset();
+  if (indef) c.cf.indefinite++;
   *its_out = its;
   *indef_out = indef;
   return J;
@@ -917,6 +959,8 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
   c.e_valid = false;
   c.u11.L.clear();
   c.h11.L.clear();
+  c.cf.reset();
+  double J_prev = HUGE_VAL;
   int prec = c.opts.prec;
   const bool mixed = prec != MPSLCC_FP64;
   GemmPrec gp(c, mixed ? MPSLCC_BF16X3 : MPSLCC_FP64);
@@ -948,6 +992,9 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
         bool indef = false;
         J = lcc_local(c, P11, P10, PS, l, prec, rprec, xb, &its, &indef);
         E2 = J;
+        // within a sweep the local minima do not rise, up to truncation effects
+        if (J > J_prev + 1e-6 * std::max(1e-12, std::fabs(J_prev))) c.cf.j_rise++;
+        J_prev = J;
         double disc;
         {
           StageTimer tm(c, &c.st.t_trunc);
@@ -998,6 +1045,12 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
   c.J = J;
   c.E2 = E2;
   c.have_E2 = true;
+  c.st.n_noconv += c.cf.noconv;
+  c.st.n_indefinite += c.cf.indefinite;
+  c.st.n_j_rise += c.cf.j_rise;
+  c.st.max_rel_residual = c.cf.max_rel_residual;
+  c.flags = (c.cf.noconv ? MPSLCC_FLAG_NOCONV : 0) | (c.cf.indefinite ? MPSLCC_FLAG_INDEFINITE : 0) |
+            (c.cf.j_rise ? MPSLCC_FLAG_J_ROSE : 0);
   return E2;
 }
 
@@ -1053,6 +1106,8 @@ void compute_energies(Ctx& c) {
   c.E3 = expect_fp64(c, &c.phi1, MPO_U, &c.phi1) - 2.0 * s * (g - h);
   c.e3_valid = true;
   c.e_valid = true;
+  if (c.E2 > 0) c.flags |= MPSLCC_FLAG_E2_POSITIVE;
+  else c.flags &= ~MPSLCC_FLAG_E2_POSITIVE;
 }
 
 void compute_e3(Ctx& c) { compute_energies(c); }

@@ -1,20 +1,25 @@
 // Tensor-core sigma path for sm_103a: a grouped GEMM whose operand tiles are
-// staged by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a 4-stage
-// shared-memory ring and multiplied by tcgen05.mma (kind::f16 with BF16
-// operands, or kind::tf32) into an FP32 accumulator in tensor memory.  One
-// thread issues TMA, one thread issues MMA, and the four warps of the CTA
-// drain the accumulator with tcgen05.ld.
+// staged by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a shared-memory
+// ring (4 stages of one A and one B tile; 2 stages in split mode, where a
+// stage holds the hi and lo tiles of both operands) and multiplied by
+// tcgen05.mma (kind::f16 with BF16 operands, or kind::tf32) into an FP32
+// accumulator in tensor memory.  One thread issues TMA, one thread issues
+// MMA, and four epilogue warps drain a double-buffered accumulator with
+// tcgen05.ld.
 //
 // Each task carries its own tensor maps, so the uneven quantum-number
 // sectors of one sigma product (every operator class, every middle sector)
 // run in one launch per phase.  The epilogue either stores rows with a
 // batched row remap (phase 1 writes the stacked T_w^T blocks) or adds FP32
 // partial sums atomically (phase 2, split over the channel dimension K).
-// Every mbarrier wait is bounded; on expiry the kernel records an error flag,
-// stops issuing work, frees its tensor memory and returns.
+// Every mbarrier wait is bounded (a launch argument); on expiry the kernel
+// records an error flag and stops issuing work, then waits (with a separate,
+// fixed bound) for the TMA loads and tensor-core products it already issued,
+// frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -47,10 +52,13 @@ struct alignas(64) TcTask {
   int batch;            // independent products of the same shape
   int a3d, b3d;         // operand map has the batch as third dimension (else shared)
   long long cbatch;     // output offset between batch entries (elements)
+  long long kstride;    // output offset between K-split partials (elements);
+                        // each split stores its own partial (mode 2)
 };
 
 namespace {
 
+constexpr int MAX_DEVICES = 128;
 constexpr int STAGES = 4;
 constexpr int A_BYTES = 128 * 128;           // 128 rows x 128 bytes
 constexpr int B_BYTES_MAX = 256 * 128;       // up to 256 rows x 128 bytes
@@ -59,7 +67,8 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int ACC_COLS = 256;                // one FP32 accumulator (N <= 256)
 constexpr int TMEM_COLS = 2 * ACC_COLS;      // double-buffered
 constexpr int TC_THREADS = 192;              // TMA warp, MMA warp, 4 epilogue warps
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s bound on every mbarrier wait
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // default bound on every mbarrier wait (2 s)
+constexpr unsigned long long DRAIN_NS = 2000000000ull;  // bound on the drain of issued work after an abort
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -99,12 +108,12 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
-__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+__device__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (gtimer() - t0 > WAIT_NS) break;
+    if (gtimer() - t0 > limit_ns) break;
     __nanosleep(32);
   }
   atomicExch(err, code);
@@ -377,7 +386,8 @@ __device__ __forceinline__ void store_row(const TcTask* T, long long roff, int c
 
 template <int PREC, bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
-                                                                 long long total, int* err) {
+                                                                 long long total, int* err,
+                                                                 unsigned long long wait_ns) {
   // Warp roles: warp 0 issues TMA, warp 1 issues MMA (and owns the tensor
   // memory), warps 2..5 drain a double-buffered accumulator, so the loads and
   // products of the next tile overlap the epilogue of the previous one.
@@ -391,7 +401,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
   uint64_t* empty = full + NST;
   uint64_t* acc_full = empty + NST;      // [2]
   uint64_t* acc_empty = acc_full + 2;    // [2]
-  volatile uint32_t* tslot = (volatile uint32_t*)(acc_empty + 2);
+  uint64_t* drain = acc_empty + 2;       // [1] completion of the MMA thread's issued products
+  volatile uint32_t* tslot = (volatile uint32_t*)(drain + 1);
   volatile int* s_abort = (volatile int*)(tslot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -404,6 +415,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
     }
+    mbar_init(drain, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -433,7 +445,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
         const uint32_t bbytes = (uint32_t)T->ntile * 128u;
         for (int j = 0; j < nk; ++j, ++it) {
           const uint32_t s = it % NST, ph = (it / NST) & 1u;
-          if (!mbar_wait(&empty[s], ph ^ 1u, err, 1)) { *s_abort = 1; break; }
+          if (!mbar_wait(&empty[s], ph ^ 1u, err, 1, wait_ns)) { *s_abort = 1; break; }
           uint8_t* st = smem + s * SB;
           const int kx = (kt0 + j) * KT;
           mbar_expect_tx(&full[s], (SPLIT ? 2u : 1u) * (A_BYTES + bbytes));
@@ -445,6 +457,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
           }
         }
       }
+      // Before the CTA exits, every TMA load this thread issued must have
+      // landed, whichever warp stopped the loop and when: only the last NST
+      // fills can still be in flight (each earlier stage was re-armed only
+      // after its previous fill had been consumed).  On the normal path all of
+      // them were consumed and these waits return at once.
+      const uint32_t first = it > (uint32_t)NST ? it - (uint32_t)NST : 0u;
+      for (uint32_t j = first; j < it; ++j) mbar_wait(&full[j % NST], (j / NST) & 1u, err, 5, DRAIN_NS);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
@@ -458,13 +477,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
         const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
         const uint32_t buf = tcount & 1u;
         const uint32_t acc = tmem + buf * ACC_COLS;
-        if (!mbar_wait(&acc_empty[buf], ((tcount >> 1) & 1u) ^ 1u, err, 4)) { *s_abort = 1; break; }
+        if (!mbar_wait(&acc_empty[buf], ((tcount >> 1) & 1u) ^ 1u, err, 4, wait_ns)) { *s_abort = 1; break; }
         fence_after();
         const uint32_t id = idesc<PREC>(128, T->ntile);
         bool ok = true;
         for (int j = 0; j < nk; ++j, ++it) {
           const uint32_t s = it % NST, ph = (it / NST) & 1u;
-          if (!mbar_wait(&full[s], ph, err, 2)) { ok = false; break; }
+          if (!mbar_wait(&full[s], ph, err, 2, wait_ns)) { ok = false; break; }
           fence_after();
           uint8_t* st = smem + s * SB;
           const uint64_t a = sdesc(st);
@@ -484,6 +503,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
         umma_commit(&acc_full[buf]);
         if (!ok) { *s_abort = 1; break; }
       }
+      // Every product this thread issued completes before tensor memory is
+      // freed and the shared-memory stages they read are released, also when
+      // an epilogue warp stopped early (on the normal path the epilogue has
+      // already waited for all of them).
+      umma_commit(drain);
+      mbar_wait(drain, 0u, err, 6, DRAIN_NS);
     }
   } else {
     // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31
@@ -497,7 +522,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
       const int row0 = tc.tmi * 128, col0 = tc.tni * T->ntile;
       const int ntile = T->ntile;
       const uint32_t buf = tcount & 1u;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (tcount >> 1) & 1u, err, 3));
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (tcount >> 1) & 1u, err, 3, wait_ns));
       if (!ok || *s_abort) { *s_abort = 1; break; }
       fence_after();
       const int row = row0 + quarter * 32 + lane;
@@ -505,7 +530,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
       const bool live = row < T->m;
       long long roff = 0;
       if (live)
-        roff = (long long)tc.b * T->cbatch + (long long)(row / T->rpb) * T->bstride + (long long)(row % T->rpb) * T->ldc;
+        roff = (long long)tc.b * T->cbatch + (long long)tc.ks * T->kstride + (long long)(row / T->rpb) * T->bstride +
+               (long long)(row % T->rpb) * T->ldc;
       for (int cb = 0; cb < ntile; cb += 32) {
         uint32_t v[32];
         tmem_ld32(taddr + cb, v);
@@ -665,11 +691,22 @@ void encode_map3d(Ctx& c, CUtensorMap* map, int prec, const void* base, long row
   MPSLCC_REQUIRE(r == CUDA_SUCCESS, ST_CUDA, "cuTensorMapEncodeTiled (3D) failed");
 }
 
-int sm_count(Ctx& c) {
-  static int n = 0;
-  if (!n) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, c.device);
-  return n > 0 ? n : 148;
+// multiprocessor count of a device (cached per device ordinal)
+int sm_count_dev(int device) {
+  static std::atomic<int> cache[MAX_DEVICES];
+  if (device < 0 || device >= MAX_DEVICES) return 152;
+  int n = cache[device].load(std::memory_order_relaxed);
+  if (n <= 0) {
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      return 152;
+    }
+    cache[device].store(n, std::memory_order_relaxed);
+  }
+  return n;
 }
+
+int sm_count(Ctx& c) { return sm_count_dev(c.device); }
 
 // C (m x n, remapped rows) op= A (m x K) B (n x K)^T.  In split mode (prec
 // BF16X3) each operand row holds the hi part at +0 and the lo part at +lo_off
@@ -677,9 +714,19 @@ int sm_count(Ctx& c) {
 // One tensor-core task C = A B^T (A m x k, B n x k, K contiguous).  With
 // batch > 1 it holds `batch` products of this shape: operand X advances by
 // x_bs elements per entry (0 = shared by all entries) and C by c_bs.
+// Number of K splits a task gets for a requested count: every split non-empty.
+int tc_ksplit(int prec, int k, int hint) {
+  const int KT = prec == MPSLCC_TF32 ? 32 : 64;
+  const int ksteps = (k + KT - 1) / KT;
+  int ks = std::max(1, std::min(hint, ksteps));
+  const int kchunk = (ksteps + ks - 1) / ks;
+  return (ksteps + kchunk - 1) / kchunk;
+}
+
 TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long ldb, int m, int n, int k, void* C,
                  int ldc, int rpb, long long bstride, int mode, int ksplit_hint, long long soff = 0,
-                 long lo_off = 0, int batch = 1, long long a_bs = 0, long long b_bs = 0, long long c_bs = 0) {
+                 long lo_off = 0, int batch = 1, long long a_bs = 0, long long b_bs = 0, long long c_bs = 0,
+                 long long kstride = 0) {
   TcTask t;
   std::memset(&t, 0, sizeof(t));
   const int KT = prec == MPSLCC_TF32 ? 32 : 64;
@@ -713,6 +760,10 @@ TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long 
   t.ksplit = std::max(1, std::min(ksplit_hint, t.ksteps));
   t.kchunk = (t.ksteps + t.ksplit - 1) / t.ksplit;
   t.ksplit = (t.ksteps + t.kchunk - 1) / t.kchunk;  // every split non-empty
+  MPSLCC_REQUIRE(t.ksplit == tc_ksplit(prec, k, ksplit_hint), ST_INTERNAL, "K split count");
+  MPSLCC_REQUIRE(t.ksplit == 1 || mode == 0 || (mode == 2 && kstride > 0), ST_INTERNAL,
+                 "split-K partials need atomic adds or a partial stride");
+  t.kstride = t.ksplit > 1 ? kstride : 0;
   t.tm = (m + 127) / 128;
   t.tn = (n + t.ntile - 1) / t.ntile;
   // output range check
@@ -725,6 +776,7 @@ TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long 
   if (mode == 3) last += soff;
   if (mode == 5) last += 5 * soff;
   last += (long long)(batch - 1) * t.cbatch;
+  last += (long long)(t.ksplit - 1) * t.kstride;
   t.soff = soff;
   c.check_bytes(C, (last + 1) * es, "tc output");
   return t;
@@ -739,28 +791,41 @@ long long plan_tc(std::vector<TcTask>& t) {
   return tot;
 }
 
+// The dynamic shared-memory opt-in is a per-device function attribute: it is
+// set once per (kernel instance, device), the flag kept per device.
 template <int P, bool S>
-void launch_variant(cudaStream_t st, int grid, const TcTask* d_tasks, int ntasks, long long total, int* err) {
-  static bool attr = false;
-  if (!attr) {
+void launch_variant(cudaStream_t st, int grid, const TcTask* d_tasks, int ntasks, long long total, int* err,
+                    unsigned long long wait_ns) {
+  static std::atomic<bool> attr[MAX_DEVICES];
+  int dev = 0;
+  cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  MPSLCC_REQUIRE(dev >= 0 && dev < MAX_DEVICES, ST_ARG, "device ordinal out of range");
+  if (!attr[dev].load(std::memory_order_acquire)) {
     cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
                "smem attr");
-    attr = true;
+    attr[dev].store(true, std::memory_order_release);
   }
-  tc_gemm_kernel<P, S><<<grid, TC_THREADS, SMEM_BYTES, st>>>(d_tasks, ntasks, total, err);
+  tc_gemm_kernel<P, S><<<grid, TC_THREADS, SMEM_BYTES, st>>>(d_tasks, ntasks, total, err, wait_ns);
 }
 
 void launch_tc_stream(cudaStream_t st, int grid, int prec, const TcTask* d_tasks, int ntasks, long long total,
-                      int* err) {
-  if (prec == MPSLCC_BF16X3) launch_variant<MPSLCC_BF16, true>(st, grid, d_tasks, ntasks, total, err);
-  else if (prec == MPSLCC_BF16) launch_variant<MPSLCC_BF16, false>(st, grid, d_tasks, ntasks, total, err);
-  else launch_variant<MPSLCC_TF32, false>(st, grid, d_tasks, ntasks, total, err);
+                      int* err, unsigned long long wait_ns = WAIT_NS) {
+  if (prec == MPSLCC_BF16X3) launch_variant<MPSLCC_BF16, true>(st, grid, d_tasks, ntasks, total, err, wait_ns);
+  else if (prec == MPSLCC_BF16) launch_variant<MPSLCC_BF16, false>(st, grid, d_tasks, ntasks, total, err, wait_ns);
+  else launch_variant<MPSLCC_TF32, false>(st, grid, d_tasks, ntasks, total, err, wait_ns);
+}
+
+// bound on each mbarrier wait of a context's tensor-core launches
+unsigned long long wait_bound_ns(const Ctx& c) {
+  const double s = c.opts.wait_timeout_s;
+  if (!(s > 0.0)) return WAIT_NS;
+  return (unsigned long long)(std::min(s, 60.0) * 1e9);
 }
 
 void launch_tc(Ctx& c, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err) {
   if (total <= 0 || ntasks <= 0) return;
   int grid = (int)std::min<long long>(total, (long long)sm_count(c));
-  launch_tc_stream(c.s(), grid, prec, d_tasks, ntasks, total, err);
+  launch_tc_stream(c.s(), grid, prec, d_tasks, ntasks, total, err, wait_bound_ns(c));
   cuda_check(cudaGetLastError(), "tc_gemm launch");
   c.st.kernel_launches++;
   c.st.gemm_launches++;
@@ -812,7 +877,11 @@ void check_err(Ctx& c, DBuf& err) {
 struct TcState {
   int layout = -1;      // operand precision class: TF32, BF16 or BF16X3 (the
                         // three-piece six-block layout, serving BF16X3 and BF16X6)
-  DBuf lcat, rstk, tt, x, y, conv, convx, err;
+  DBuf lcat, rstk, tt, x, conv, convx, err;
+  // phase-2 K-split partials (FP32) and the segments of their fixed-order sum
+  DBuf ypart[2], segs[2];
+  int nseg[2] = {0, 0};
+  long long seg_tiles[2] = {0, 0};
   std::vector<long> lcat_off, K8, tt_off, x_off;
   std::vector<long> stk_off;
   std::vector<ConvTask> xconv;
@@ -895,7 +964,6 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   zalloc(S->rstk, ssz, es);
   zalloc(S->tt, tsz, es);
   zalloc(S->x, xsz, es);
-  zalloc(S->y, std::max(P.nb, 1L), 4);
   zalloc(S->err, 4, 1);
   // FP64 -> low precision copies of L' (A side of phase 2) and R' (A side of
   // phase 1)
@@ -980,7 +1048,10 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
       S->bytes1[v] += (double)es * pcs * ((double)st.nw * rb * rk + (double)lk * rk + (double)st.nw * rb * lk);
     }
     // phase 2: sigma = Lcat Tt^T, split over K so that every tile carries
-    // about the same number of K steps (a balanced persistent schedule)
+    // about the same number of K steps (a balanced persistent schedule).
+    // Split j of a middle sector stores its FP32 partial at its own offset;
+    // one reduction sums the partials in increasing j into the FP64 sigma,
+    // so the result does not depend on the order the splits finish in.
     long long work = 0;
     for (size_t bi = 0; bi < nbk; ++bi) {
       if (S->K8[bi] == 0) continue;
@@ -990,18 +1061,49 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
       work += (long long)((lb + 127) / 128) * ((rb + nt - 1) / nt) * ((kk + 63) / 64);
     }
     const long long kper = std::max(4LL, (work + 4 * target - 1) / (4 * target));
+    std::vector<SplitSeg> segs;
+    std::vector<int> ksv(nbk, 0);
+    long poff = 0;
+    for (size_t bi = 0; bi < nbk; ++bi) {
+      const int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+      SplitSeg sg;
+      std::memset(&sg, 0, sizeof(sg));
+      sg.out_off = P.off_b[bi];
+      sg.m = lb;
+      sg.n = rb;
+      sg.ldp = (int)((rb + 3) / 4 * 4);   // 16-byte aligned partial rows
+      sg.sstride = (long long)lb * sg.ldp;
+      if (S->K8[bi] > 0) {
+        const long pitch = sp * S->K8[bi];
+        const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
+        const int hint = (int)std::max(1LL, (((long long)kk + 63) / 64 + kper - 1) / kper);
+        ksv[bi] = tc_ksplit(kp, kk, hint);
+        sg.nsplit = ksv[bi];
+        sg.part_off = poff;
+        poff += (long)ksv[bi] * sg.sstride;
+      }
+      segs.push_back(sg);   // nsplit = 0: no channel reaches the sector, sigma is zero there
+    }
+    S->ypart[v].alloc(&c, std::max<long>(poff, 4) * 4);
     for (size_t bi = 0; bi < nbk; ++bi) {
       if (S->K8[bi] == 0) continue;
       int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
       const long pitch = sp * S->K8[bi];
       const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
-      int ks = (int)std::max(1LL, (((long long)kk + 63) / 64 + kper - 1) / kper);
+      const SplitSeg& sg = segs[bi];
       t2.push_back(make_task(c, kp, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, pitch,
                              (char*)S->tt.p + (size_t)S->tt_off[bi] * es, pitch, lb, rb, kk,
-                             (float*)S->y.p + P.off_b[bi], rb, 1 << 30, 0, 0, ks, 0,
-                             (six && v == 0) ? 2 * S->K8[bi] : 0));
+                             (float*)S->ypart[v].p + sg.part_off, sg.ldp, 1 << 30, 0, 2, ksv[bi], 0,
+                             (six && v == 0) ? 2 * S->K8[bi] : 0, 1, 0, 0, 0, sg.sstride));
       S->bytes2[v] += (double)es * pcs * ((double)lb * S->K8[bi] + (double)rb * S->K8[bi]) + 4.0 * lb * rb;
     }
+    S->nseg[v] = (int)segs.size();
+    S->seg_tiles[v] = plan_split_tiles(segs.data(), (int)segs.size());
+    S->segs[v].alloc(&c, std::max<size_t>(segs.size(), 1) * sizeof(SplitSeg));
+    if (!segs.empty())
+      cuda_check(cudaMemcpyAsync(S->segs[v].p, segs.data(), segs.size() * sizeof(SplitSeg), cudaMemcpyHostToDevice,
+                                 c.s()),
+                 "split segments");
     S->n1[v] = (int)t1.size();
     S->n2[v] = (int)t2.size();
     S->tiles1[v] = plan_tc(t1);
@@ -1027,13 +1129,14 @@ void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
     cuda_check(cudaMemcpyAsync(P.xin.p, x, P.nk * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma in");
   std::vector<ConvTask> xc = S->xconv;
   run_conv(c, S->layout, xc, S->convx);
-  cuda_check(cudaMemsetAsync(S->y.p, 0, std::max(P.nb, 1L) * 4, c.s()), "sigma zero");
   cudaEventRecord(c.ev_p0, c.s());
   launch_tc(c, kp, (const TcTask*)S->t1[v].p, S->n1[v], S->tiles1[v], (int*)S->err.p);
   cudaEventRecord(c.ev_p1, c.s());
   launch_tc(c, kp, (const TcTask*)S->t2[v].p, S->n2[v], S->tiles2[v], (int*)S->err.p);
   cudaEventRecord(c.ev_p2, c.s());
-  launch_f32_to_f64(P.nb, (const float*)S->y.p, y, c.s());
+  launch_splitk_reduce_f32((const SplitSeg*)S->segs[v].p, S->nseg[v], S->seg_tiles[v], (const float*)S->ypart[v].p, y,
+                           c.s());
+  cuda_check(cudaGetLastError(), "split-K reduction");
   c.st.kernel_launches++;
   check_err(c, S->err);
   float m1 = 0, m2 = 0;
@@ -1117,13 +1220,13 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH
 
 namespace {
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[128] = {};
+void* g_noalloc_ptr[MAX_DEVICES] = {};
 
 // Device address of the scratch array for the current device (host code sees
 // only a host-side stand-in for the symbol, so it must be looked up per device).
 void* noalloc_scratch(int device) {
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  MPSLCC_REQUIRE(device >= 0 && device < 128, ST_ARG, "device ordinal out of range");
+  MPSLCC_REQUIRE(device >= 0 && device < MAX_DEVICES, ST_ARG, "device ordinal out of range");
   if (!g_noalloc_ptr[device]) {
     void* p = nullptr;
     cuda_check(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress");
@@ -1216,7 +1319,7 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
   t.batch = 1;
   long long tiles = (long long)t.tm * t.tn;
   cuda_check(cudaMemcpyAsync(base + o_task, &t, sizeof(t), cudaMemcpyHostToDevice, stream), "noalloc task");
-  int grid = (int)std::min<long long>(tiles, 148);
+  int grid = (int)std::min<long long>(tiles, sm_count_dev(device));
   launch_tc_stream(stream, grid, prec, (const TcTask*)(base + o_task), 1, tiles, (int*)(base + o_err));
   cuda_check(cudaGetLastError(), "noalloc gemm");
   launch_f32_to_f64((long)m * n, (const float*)(base + o_c), dC, stream);

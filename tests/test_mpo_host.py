@@ -173,3 +173,22 @@ def test_binding_structs_match_header_layout(mpslcc, cname, pyname, tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert got[0] == ctypes.sizeof(py)
     assert got[1:] == [getattr(py, f).offset for f in fields]
+
+
+def test_non_finite_integrals_are_rejected(mpslcc):
+    """A NaN or infinity in h or V is an argument error; the context keeps
+    working afterwards."""
+    h, V = _integrals(3, 4)
+    ctx = mpslcc.Context(device=-1)
+    for bad in ("h", "V"):
+        hb, Vb = h.copy(), V.copy()
+        if bad == "h":
+            hb[1, 1] = np.nan
+        else:
+            Vb[0, 0, 0, 0] = np.inf
+        with pytest.raises(mpslcc.MpsLccError) as e:
+            ctx.build_mpo(hb, Vb, n_elec=2, two_sz=0)
+        assert e.value.status == 1 and "non-finite" in str(e.value)
+    ctx.build_mpo(h, V, n_elec=2, two_sz=0)
+    assert len(ctx.mpo_bond_dims(mpslcc.MPO_H)) == 4
+    ctx.close()

@@ -16,6 +16,30 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5  # relative, the FP32-output tolerance of the tensor-core tests
 
 
+def _bf16(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _tf32(x):
+    """Operand as the tensor core reads it: FP32 with the low 13 mantissa bits dropped."""
+    f = np.asarray(x, dtype=np.float32)
+    return (f.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32).astype(np.float64)
+
+
+def _rounded_product(prec_name, A, B):
+    """The product the tensor cores compute, from operands rounded on the host:
+    BF16 and TF32 round each operand once; BF16X3 keeps about 16 bits of each."""
+    if prec_name == "BF16":
+        return _bf16(A) @ _bf16(B).T, TOL
+    if prec_name == "TF32":
+        return _tf32(A) @ _tf32(B).T, TOL
+    return A @ B.T, 2e-5
+
+
 @pytest.mark.parametrize("prec_name,m,n,k", [("BF16", 130, 144, 136), ("TF32", 257, 40, 700),
                                              ("BF16X3", 300, 96, 520)])
 def test_noalloc_gemm_matches_allocating_entry_point(mpslcc, prec_name, m, n, k):
@@ -30,6 +54,7 @@ def test_noalloc_gemm_matches_allocating_entry_point(mpslcc, prec_name, m, n, k)
     dA = torch.from_numpy(A).cuda()
     dB = torch.from_numpy(B).cuda()
     stream = torch.cuda.current_stream().cuda_stream
+    direct, dtol = _rounded_product(prec_name, A, B)
     for call in range(2):  # two calls in a row share the scratch array
         dC = torch.full((m, n), float("nan"), dtype=torch.float64, device="cuda")
         mpslcc.tc_gemm_noalloc(0, stream, prec, m, n, k, dA.data_ptr(), dB.data_ptr(), dC.data_ptr())
@@ -37,6 +62,9 @@ def test_noalloc_gemm_matches_allocating_entry_point(mpslcc, prec_name, m, n, k)
         C = dC.cpu().numpy()
         err = np.abs(C - ref).max() / np.abs(ref).max()
         assert err <= TOL, (call, err)
+        # and against the product of host-rounded operands, independent of the library
+        err_d = np.abs(C - direct).max() / np.abs(direct).max()
+        assert err_d <= dtol, (call, err_d)
 
 
 def test_noalloc_gemm_rejects_oversized_problem(mpslcc):
