@@ -15,7 +15,10 @@ holes), reference M0 = 500, first-order M1 = 2000, tensor-core sigma products
 Printed metric: sigma-vector TFLOP/s over the timed sweeps (algorithmic flops
 of every sigma product divided by the device time of the whole sweeps), plus
 the sweep seconds and the energies.  ``--impl reference`` times the CPU oracle
-instead (see ``cpu_sample``).
+instead (``oracle.blocksparse`` sigma on the workload's sample, see
+``_o2_workload``); the same oracle sample is the line's ``cpu_baseline``.  By
+default the line also compares mixed precision with the plain FP64 path on a
+window of middle positions from the same states (``fp64_compare``).
 """
 from __future__ import annotations
 
@@ -26,7 +29,6 @@ import os
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -58,6 +60,9 @@ def parse():
                     help="also time one sweep on the plain FP64 path from the same states (about 8 minutes "
                          "at M1 = 2000)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the mixed-vs-FP64 comparison on a window of middle positions")
+    ap.add_argument("--compare-window", type=int, default=4)
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="profiling mode: N sigma products at the middle position inside NVTX range 'sigma'")
     return ap.parse_args()
@@ -127,41 +132,67 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def cpu_sample(budget_s):
-    """Time the CPU oracle's local problem: sigma = P^T H0 P psi built densely
-    in the determinant space (Implementation section, Fig. 3).  The oracle
-    holds at most ~10^4 determinants, so the sample is the L=8 chain
-    workload (4900 determinants, a random M=64 first-order MPS) rather than
-    the 24-orbital workload; flops are counted with the library's sigma
-    accounting for the same local problem."""
+def _o2_workload(cfg, M1):
+    """The CPU oracle's sample of the workload: its own MPO of H0 (built from
+    the integrals alone), a random block-sparse MPS with the workload's
+    orbitals, electrons and bond-dimension budget, the middle two-site
+    position, random environment blocks of the MPO's channel classes (the
+    cost of a sigma does not depend on the values) and a random vector."""
     import numpy as np
 
     import synth
-    from oracle import fci, mps as omps
-    c = synth.config(0)
-    dets = fci.determinants(8, 4, 4)
-    H = fci.build_hamiltonian(c["h"], c["V"], dets)
-    H0 = fci.fink_h0(H, dets, 8, c["n_core"], c["n_active"])
-    m = synth.random_mps(8, 8, 0, M=64, seed=5)
-    l = 3
-    n = len(omps.local_layout(m, l)[0])
-    psi = synth.random_vector(n, 1)
+    from oracle import blocksparse as bs
+    c = synth.config(cfg)
+    k = c["n_orb"]
+    mpo = bs.Mpo(c["h"], c["V"], "H0", c["n_core"], c["n_active"])
+    m = synth.random_mps(k, c["n_alpha"] + c["n_beta"], 0, M=M1, seed=5)
+    l = k // 2 - 1
+    rng = np.random.default_rng(11)
+
+    def env(b):
+        out = {}
+        bond = m["bonds"][b]
+        for ib, (nb, zb, db) in enumerate(bond):
+            for ik, (nk, zk, dk) in enumerate(bond):
+                cl = mpo.class_of(b, (nb - nk, zb - zk))
+                if cl >= 0:
+                    out[(ib, ik)] = rng.standard_normal((mpo.class_n[b][cl], db, dk))
+        return out
+
+    L, R = env(l), env(l + 2)
+    _, _, n = bs.local_blocks(m, l)
+    psi = synth.random_vector(n, 3)
+    classes = dict(zip(mpo.bond_classes[l + 1], mpo.class_n[l + 1]))
+    return dict(mpo=mpo, mps=m, l=l, L=L, R=R, psi=psi, n=n, flops=sigma_flops(m, l, classes), name=c["name"])
+
+
+def o2_sigma_seconds(w, budget_s):
+    """Times the oracle's sigma (oracle.blocksparse.sigma) on workload sample
+    w until budget_s has passed (at least one product)."""
+    from oracle import blocksparse as bs
     t0 = time.perf_counter()
     steps = 0
     while True:
-        Heff = omps.effective_hamiltonian(m, l, H0, dets)
-        _ = Heff @ psi
+        bs.sigma(w["mpo"], w["mps"], w["mps"], w["l"], w["psi"], w["L"], w["R"])
         steps += 1
         if time.perf_counter() - t0 > budget_s:
             break
-    dt = (time.perf_counter() - t0) / steps
-    return dict(seconds_per_sigma=dt, steps=steps, n_local=n, mps=m, l=l)
+    return (time.perf_counter() - t0) / steps, steps
 
 
-def sigma_flops_host(mps, l, mpo_class_sizes):
-    """Library's algorithmic flop count of one sigma (two phases) for bra =
-    ket = mps at position l; mpo_class_sizes maps the class quantum-number
-    change (dN, d2Sz) to the number of channels on the middle MPO bond."""
+def o2_description(w, M1):
+    return (f"CPU oracle (oracle.blocksparse, FP64 numpy/OpenBLAS) sigma of H0 at the middle position l={w['l']} "
+            f"of {w['name']}: random block-sparse MPS with the workload's orbitals, electrons and M1={M1} sector "
+            f"budget (n_local={w['n']}), random environment blocks of the oracle's own MPO classes; flops = the "
+            f"two-phase sigma accounting of the same sector tables ({w['flops']:.3e} per sigma)")
+
+
+def sigma_flops(mps, l, mpo_class_sizes):
+    """Algorithmic flops of one sigma (bra = ket = mps, position l): phase 1
+    T_w^T = R'_w psi^T summed over the channel classes of the middle MPO
+    bond, phase 2 sigma = [L'_w ...][T_w; ...] with K = sum over classes of
+    channels x ket fused-left dimension.  mpo_class_sizes maps the class
+    quantum-number change (dN, d2Sz) to its channel count."""
     LQ = [(0, 0), (1, 1), (1, -1), (2, 0)]
 
     def fl(bond, mask):
@@ -203,67 +234,87 @@ def workload_config(c, M0, M1, world):
 
 
 def reference_arm(args, rank, world):
+    """The CPU oracle timed on the host cores: every step is one sigma of the
+    oracle's block-sparse contraction on the workload sample (rank 0 only)."""
     if rank != 0:
         return
-    import paper_1509_00216_gb300 as mp  # host-only context: MPO class sizes for the flop count
     import synth
-    wc = synth.config(args.config)
-    c = synth.config(0)
-    ctx = mp.Context(device=-1)
-    ctx.build_mpo(c["h"], c["V"], 8, 0)
-    ctx.set_spaces(c["n_core"], c["n_active"])
-    idx, _ = None, None
-    s = None
-    times = []
-    for i in range(args.warmup + args.steps):
-        s = cpu_sample(max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup)))
-        if i >= args.warmup:
-            times.append(s["seconds_per_sigma"])
-    # class sizes of the H0 MPO on the middle bond of position l
-    classes = _mpo_classes(ctx, mp.MPO_H0, s["l"] + 1)
-    ctx.close()
-    f = sigma_flops_host(s["mps"], s["l"], classes)
-    dt = sum(times) / len(times)
-    v = f / dt / 1e12
+    c = synth.config(args.config)
+    M0, M1 = args.M0 or c["M0"], args.M1 or c["M1"]
+    w = _o2_workload(args.config, M1)
+    for _ in range(args.warmup):
+        o2_sigma_seconds(w, 0.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o2_sigma_seconds(w, 0.0)
+    dt = (time.perf_counter() - t0) / args.steps
+    v = w["flops"] / dt / 1e12
     cores = os.cpu_count()
     line = dict(metric=METRIC, value=v, unit="TFLOP/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=dt * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
-                data="synthetic", impl="reference",
-                config=workload_config(wc, args.M0 or wc["M0"], args.M1 or wc["M1"], world),
+                data="synthetic", impl="reference", config=workload_config(c, M0, M1, world),
                 cpu_baseline={"value": v, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
-                              "sample": "dense determinant-space P^T H0 P psi at position 3 of a random "
-                                        "M=64 MPS of the L=8 chain (4900 determinants): the oracle cannot "
-                                        "hold the 24-orbital workload, so this local sigma stands in for it; "
-                                        "flops = library sigma accounting"},
+                              "sample": "one sigma per step; " + o2_description(w, M1)},
                 e2e={"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
     print(json.dumps(line), flush=True)
 
 
-def _mpo_classes(ctx, which, bond):
-    """Channel counts per quantum-number class of one MPO bond (from the
-    exported site tensor's right channels)."""
-    import numpy as np
-    idx, val = ctx.export_mpo_site(which, bond - 1)
-    LQ = [(0, 0), (1, 1), (1, -1), (2, 0)]
-    # propagate channel QN changes from the left boundary
-    k = ctx.n_orb
-    dq = {0: (0, 0)}
-    for p in range(bond):
-        ii, _ = ctx.export_mpo_site(which, p)
-        nd = {}
-        for (w0, w1, so, si) in ii:
-            if w0 in dq and w1 not in nd:
-                a = dq[w0]
-                nd[w1] = (a[0] + LQ[so][0] - LQ[si][0], a[1] + LQ[so][1] - LQ[si][1])
-        dq = nd
-    out = {}
-    for w, q in dq.items():
-        out[q] = out.get(q, 0) + 1
-    return out
-
-
-SIGMA_TRAFFIC_RATIO = (3.270 + 3.547) / (2.512 + 2.690)
 METRIC = "sigma-vector TFLOP/s and LCC sweep s at M=2000, mixed vs FP64; |dE| vs oracle"
+
+
+def fp64_compare(mp, mx, c, M0, M1, prec, local_rank, window, torch):
+    """Mixed precision against the plain FP64 path on representative positions
+    (the FP64 sweep at this size takes minutes): from the converged states the
+    mixed context first moves Phi1's orthogonality centre to the middle
+    window's first position; then the same window of two-site steps runs from
+    the same states in FP64 and in mixed precision.  Reports both window
+    times, the window's sigma flops, the FP64 sweep time extrapolated by
+    flops from the mixed sweep's sigma flops, and the energy differences of
+    the resulting states (all energies are FP64 evaluations)."""
+    k = c["n_orb"]
+    first = k // 2 - window // 2 - 1
+    stream = torch.cuda.current_stream()
+    mx.lcc_window(M1, 0, first, 1)
+    p0, p1 = mx.export_mps(0), mx.export_mps(1)
+    out = {"positions": list(range(first, first + window)), "direction": "left to right"}
+
+    def run(ctx, label):
+        ctx.load_mps(0, p0)
+        ctx.dmrg_reference(M0, 0)
+        ctx.load_mps(1, p1)
+        # environments of the window's first position are in place before the
+        # timed steps, as they are inside a sweep
+        for op in (mp.OP_H0_11, mp.OP_H_10, mp.OP_S_10):
+            n_out, n_in = ctx.local_dim(first, op)
+            x = torch.zeros(n_in, dtype=torch.float64, device="cuda")
+            y = torch.empty(n_out, dtype=torch.float64, device="cuda")
+            ctx.apply_heff_device(first, op, x.data_ptr(), y.data_ptr(), n_in, n_out, mp.FP64)
+        ctx.reset_stats()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.lcc_window(M1, first, window, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = ctx.stats()
+        e = ctx.energy()
+        out[label + "_window_s"] = e0.elapsed_time(e1) * 1e-3
+        out[label + "_window_sigma_flops"] = st["sigma_flops"]
+        return e
+
+    e_mx = run(mx, "mixed")
+    c64 = mp.Context(device=local_rank, prec=mp.FP64, tol=1e-8, max_iter=60, torch_memory=True)
+    c64.build_mpo(c["h"], c["V"], c["n_alpha"] + c["n_beta"], 0)
+    c64.set_spaces(c["n_core"], c["n_active"])
+    e_64 = run(c64, "fp64")
+    c64.close()
+    out["window_speedup"] = out["fp64_window_s"] / out["mixed_window_s"]
+    for key in ("E0", "E2", "E3"):
+        out["dE_" + key] = abs(e_mx[key] - e_64[key])
+    out["energies_fp64"] = {key: e_64[key] for key in ("E0", "E2", "E3")}
+    out["energies_mixed"] = {key: e_mx[key] for key in ("E0", "E2", "E3")}
+    return out
 
 
 def gpu_arm(args, rank, world, local_rank):
@@ -320,76 +371,87 @@ def gpu_arm(args, rank, world, local_rank):
         ctx.close()
         return
     ctx.reset_stats()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flops = 0.0
+    sweep_sigma_s = 0.0
+    sweep_calls = 0
+    tc = {"s": 0.0, "b": 0.0, "s1": 0.0, "b1": 0.0, "s2": 0.0, "b2": 0.0, "n": 0}
     if dist:
         td.barrier()
     torch.cuda.synchronize()
     with Clocks(local_rank) as clk:
         torch.cuda.nvtx.range_push("timed")
         t0 = time.perf_counter()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            ctx.lcc_sweep(M1, 1)      # E2 (8 bytes) is read back to the host by every call
-        ev1.record(stream)
+        for i in range(args.steps):
+            # one step as a user runs it through the public calls: a sweep
+            # (device-timed), then the FP64 energies of its states read back
+            # to the host (the sweep's inputs -- integrals, MPO, reference --
+            # stay on the device from the set-up: no per-step host copies)
+            evs[i][0].record(stream)
+            ctx.lcc_sweep(M1, 1)
+            evs[i][1].record(stream)
+            s1 = ctx.stats()
+            flops += s1["last_sweep_sigma_flops"]
+            sweep_sigma_s += s1["last_sweep_sigma_seconds"]
+            sweep_calls += s1["last_sweep_sigma_calls"]
+            tc["s1"], tc["b1"] = s1["tc_phase1_seconds"], s1["tc_phase1_bytes"]
+            tc["s2"], tc["b2"] = s1["tc_phase2_seconds"], s1["tc_phase2_bytes"]
+            tc["n"] = s1["tc_launches"]
+            e = ctx.energy()
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
         torch.cuda.nvtx.range_pop()
+    dev_s = sum(a.elapsed_time(b) for a, b in evs) * 1e-3
+    st = ctx.stats()
+    flops2 = flops
+    d2h = 8 + 80  # E2 of the sweep call + the energies struct, per step
     if dist:
         td.barrier()
-    dev_s = ev0.elapsed_time(ev1) * 1e-3
-    st = ctx.stats()
-    flops = st["sigma_flops"]
-    flops2 = flops
-    e = ctx.energy()
     if dist:
         t = torch.tensor([dev_s, e2e_s], device="cuda")
         td.all_reduce(t, op=td.ReduceOp.MAX)
         dev_s, e2e_s = t.tolist()
     pk = peaks()
-    kern = st["sigma_seconds"]
+    kern = sweep_sigma_s
     if prec == 0:
         # FP64 DFMA path: ALU-bound against the FP64 pipe
         roof = {"bound": "alu", "achieved": flops / kern / 1e12 if kern else None, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "kernel": "gemm_f64_kernel (sigma phases)"}
     else:
-        # tensor-core sigma GEMMs run at ~55 flop/byte, far below the BF16
-        # ridge (~250): they are bounded by HBM bandwidth.  Algorithmic bytes
-        # = operands read once + results written (hi + lo pieces in split mode)
-        tcs = st["tc_phase1_seconds"] + st["tc_phase2_seconds"]
-        tcb = st["tc_phase1_bytes"] + st["tc_phase2_bytes"]
-        launches = max(1, st["tc_launches"])
+        # tensor-core sigma GEMMs run far below the BF16 ridge (about 100
+        # algorithmic flop per byte against ~280): they are bounded by HBM
+        # bandwidth.  Algorithmic bytes = operands read once + results written
+        # (every BF16 piece of the split operands)
+        tcs = tc["s1"] + tc["s2"]
+        tcb = tc["b1"] + tc["b2"]
+        launches = max(1, tc["n"])
         roof = {"bound": "hbm", "achieved": tcb / tcs / 1e9 if tcs else None, "peak": pk["hbm"], "unit": "GB/s",
-                "kernel": "tc_gemm_kernel (both sigma phases)", "launches": st["tc_launches"],
+                "kernel": "tc_gemm_kernel (both sigma phases)", "launches": tc["n"],
                 "bytes_per_launch": tcb / launches, "us_per_launch": tcs / launches * 1e6,
-                "phase1_gbs": st["tc_phase1_bytes"] / st["tc_phase1_seconds"] / 1e9 if st["tc_phase1_seconds"] else None,
-                "phase2_gbs": st["tc_phase2_bytes"] / st["tc_phase2_seconds"] / 1e9 if st["tc_phase2_seconds"] else None,
+                "phase1_gbs": tc["b1"] / tc["s1"] / 1e9 if tc["s1"] else None,
+                "phase2_gbs": tc["b2"] / tc["s2"] / 1e9 if tc["s2"] else None,
                 "tensor_tflops": flops / tcs / 1e12 if tcs else None,
                 "tensor_frac_of_bf16_sustained": flops / tcs / 1e12 / pk["bf16_sust"] if tcs else None}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
-    if prec != 0:
-        # DRAM bytes per algorithmic byte of the sigma launches, from one ncu
-        # capture of both phases at the middle position of the 3-band workload
-        # at M1 = 1000 (3.270 + 3.547 GB against 2.512 + 2.690 GB); the traffic
-        # of a launch scales with the bytes it moves, so the full-size figure
-        # is this ratio times the algorithmic bytes per launch
-        roof["traffic"] = SIGMA_TRAFFIC_RATIO * roof["bytes_per_launch"]
-        roof["traffic_source"] = "ncu dram bytes ratio 1.31 at M1=1000, scaled to the launch's algorithmic bytes"
-    else:
-        roof["traffic"] = None
+    # DRAM bytes of the counted launches come from an ncu capture of the
+    # kernel as it stands; none is taken inside this run
+    roof["traffic"] = None
     roof["peak_source"] = pk["src"]
     value = world * flops / dev_s / 1e12
     line = dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=dev_s / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype={0: "f64", 1: "tf32", 2: "bf16", 3: "bf16x3"}[prec], data="synthetic",
                 config=workload_config(c, M0, M1, world),
-                sweep_s=dev_s / args.steps, sigma_calls=st["sigma_calls"], sigma_kernel_s=kern,
+                sweep_s=dev_s / args.steps, sigma_calls=sweep_calls, sigma_kernel_s=kern,
                 stage_s={k: st[k] for k in ("t_plan", "t_rhs", "t_solve", "t_trunc", "t_env", "t_fuse_left", "t_fuse_right", "t_tc_prepare")},
                 fused_ahead={"used": st["ahead_used"], "missed": st["ahead_missed"]},
-                energies={k: e[k] for k in ("E0", "E2", "E3", "E_lcc2", "E_lcc3", "max_discarded_weight")},
+                energies={k: e[k] for k in ("E0", "E2", "E3", "E_lcc2", "E_lcc3", "max_discarded_weight", "flags")},
+                solver={"noconv": st["n_noconv"], "indefinite": st["n_indefinite"], "j_rise": st["n_j_rise"],
+                        "max_rel_residual": st["max_rel_residual"]},
                 roofline=roof, gpu_launches=st["kernel_launches"],
                 e2e={"value": world * flops2 / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
-                     "d2h_bytes_per_step": 8})
+                     "d2h_bytes_per_step": d2h, "s_per_step": e2e_s / args.steps,
+                     "what": "public calls per step: mpslcc_lcc_sweep then mpslcc_energy (FP64 energies read back)"})
     clk_s = clk.summary()
     if clk_s:
         line["clocks"] = clk_s
@@ -397,42 +459,48 @@ def gpu_arm(args, rank, world, local_rank):
         with open(args.save_state, "wb") as f:
             pickle.dump({"phi0": ctx.export_mps(0), "phi1": ctx.export_mps(1)}, f, protocol=4)
     if args.fp64_sweep and prec != 0:
-        # the same sweep on the plain FP64 path (DFMA GEMMs), from the same
-        # reference and first-order states, outside the timed region
+        # one whole sweep on the plain FP64 path (DFMA GEMMs) and one in mixed
+        # precision, both from the timed sweeps' final states, outside the
+        # timed region; times and the energies of the resulting states
         p0, p1 = ctx.export_mps(0), ctx.export_mps(1)
-        ctx.close()
+        full = {}
         c64 = mp.Context(device=local_rank, prec=mp.FP64, tol=1e-8, max_iter=60, torch_memory=True)
         c64.build_mpo(c["h"], c["V"], c["n_alpha"] + c["n_beta"], 0)
         c64.set_spaces(c["n_core"], c["n_active"])
-        c64.load_mps(0, p0)
-        c64.dmrg_reference(M0, 0)
-        c64.load_mps(1, p1)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        c64.lcc_sweep(M1, 1)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        f64_s = f0.elapsed_time(f1) * 1e-3
+        for label, cx in (("fp64", c64), ("mixed", ctx)):
+            cx.load_mps(0, p0)
+            cx.dmrg_reference(M0, 0)
+            cx.load_mps(1, p1)
+            torch.cuda.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            cx.lcc_sweep(M1, 1)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            full[label + "_sweep_s"] = f0.elapsed_time(f1) * 1e-3
+            full[label + "_energies"] = {key: cx.energy()[key] for key in ("E0", "E2", "E3")}
         c64.close()
-        line["fp64_sweep_s"] = f64_s
-        line["sweep_speedup_vs_fp64"] = f64_s / (dev_s / args.steps)
+        full["sweep_speedup_vs_fp64"] = full["fp64_sweep_s"] / full["mixed_sweep_s"]
+        for key in ("E0", "E2", "E3"):
+            full["dE_" + key] = abs(full["fp64_energies"][key] - full["mixed_energies"][key])
+        line["fp64_full_sweep"] = full
+    if not args.no_fp64_compare and prec != 0:
+        cmp_ = fp64_compare(mp, ctx, c, M0, M1, prec, local_rank, args.compare_window, torch)
+        win = cmp_["mixed_window_sigma_flops"]
+        if win > 0:
+            cmp_["fp64_sweep_s_extrapolated"] = cmp_["fp64_window_s"] * (st["last_sweep_sigma_flops"] / win)
+            cmp_["sweep_speedup_vs_fp64_extrapolated"] = cmp_["fp64_sweep_s_extrapolated"] / (dev_s / args.steps)
+        cmp_["how"] = ("same window of two-site steps from the same states on both paths; FP64 sweep time "
+                       "extrapolated from the window by the mixed sweep's sigma flops")
+        line["fp64_compare"] = cmp_
     ctx.close()
     if rank == 0:
         if not args.no_cpu_baseline:
-            s = cpu_sample(args.cpu_seconds)
-            hc = mp.Context(device=-1)
-            c0 = synth.config(0)
-            hc.build_mpo(c0["h"], c0["V"], 8, 0)
-            hc.set_spaces(c0["n_core"], c0["n_active"])
-            cls = _mpo_classes(hc, mp.MPO_H0, s["l"] + 1)
-            hc.close()
-            f = sigma_flops_host(s["mps"], s["l"], cls)
-            line["cpu_baseline"] = {"value": f / s["seconds_per_sigma"] / 1e12, "unit": "TFLOP/s",
-                                    "cores": os.cpu_count(), "kind": "oracle",
-                                    "sample": f"{s['steps']} dense P^T H0 P psi on the L=8 chain local problem "
-                                              f"(n_local={s['n_local']}); the oracle cannot hold 24 orbitals"}
+            w = _o2_workload(args.config, M1)
+            sec, n = o2_sigma_seconds(w, args.cpu_seconds)
+            line["cpu_baseline"] = {"value": w["flops"] / sec / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": f"{n} sigma products; " + o2_description(w, M1)}
         print(json.dumps(line), flush=True)
     if dist:
         td.destroy_process_group()

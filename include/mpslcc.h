@@ -219,10 +219,31 @@ mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, doubl
    minimising J = <Phi1|Q(H0-E0)Q|Phi1> - 2<Phi1|b>, b = -Q H Phi0, with
    n_sweeps two-site sweeps; local linear solves by CG / MINRES with the
    precision of opts.prec for inner products and FP64 residuals.  Writes E2
-   (the final Hylleraas value) to *E2_out.  order must be 1 (higher orders
-   return E_ARG).  The first call initialises Phi1 from opts.seed; later
-   calls continue from the current Phi1. */
+   (the final Hylleraas value) to *E2_out.  The first call initialises Phi1
+   from opts.seed; later calls continue from the current Phi1.
+   order = n >= 2 (at most 8; Eq. 1 for n > 1): sweeps the order-n
+   wavefunction Phi(n) (one MPS of bond dimension M1, initialised at the
+   first call) by minimising <x|Q(H0-E0)Q|x> - 2<x|b_n> with
+   b_n = -Q U Phi(n-1) + sum_{k=2..n-1} E(k) Q Phi(n-k), the E(k) from
+   mpslcc_energy_series of the lower orders; needs Phi(n-1) (E_STATE
+   otherwise) and writes the last local Hylleraas value to *E2_out.  The
+   reference component <Phi0|Phi(n-1)> Phi0 of a truncated lower order
+   (about 1e-8) is not projected from the U term.  Sweeping order n discards
+   the wavefunctions of orders above n. */
 mpslcc_status mpslcc_lcc_sweep(mpslcc_ctx* ctx, int M1, int order, int n_sweeps, double* E2_out);
+
+/* A window of a half sweep of mpslcc_lcc_sweep (Implementation section: the
+   sweep optimises one position at a time): `count` two-site steps starting
+   at position `first` (0..n_orb-2) and moving towards higher (dir = +1) or
+   lower (dir = -1) positions, each a local linear solve, truncation to M1
+   and environment update.  The local matrix is the LCC matrix only when
+   `first` is the orthogonality centre of Phi1: position 0 after a full sweep
+   (or a loaded state exported after one), or the position next to where a
+   previous window in the same direction ended.  Used to time and compare
+   precisions on representative positions.  Writes the last local Hylleraas
+   value to *J_out.  Errors and E_NOCONV as mpslcc_lcc_sweep. */
+mpslcc_status mpslcc_lcc_sweep_window(mpslcc_ctx* ctx, int M1, int order, int first, int count, int dir,
+                                      double* J_out);
 
 /* Eq. 1b and Eq. 2 (n = 1): energies of the current states, evaluated in
    FP64 from the MPS tensors as they are (after sweeps, or as loaded with
@@ -230,6 +251,15 @@ mpslcc_status mpslcc_lcc_sweep(mpslcc_ctx* ctx, int M1, int order, int n_sweeps,
    Hylleraas value E2 = J(Q Phi1) and E3 = <Q Phi1|U|Q Phi1>.  Needs E0
    (mpslcc_dmrg_reference); E2 / E3 are 0 while no Phi1 is present. */
 mpslcc_status mpslcc_energy(mpslcc_ctx* ctx, mpslcc_energies* out);
+
+/* Eq. 2 (Wigner 2n+1 rule): energy series E(0), E(1), ..., E(2N+1) of the
+   current wavefunctions Phi(1..N) (N = highest order present), evaluated in
+   FP64 with every Phi(n) projected as Q Phi(n) = Phi(n) - <Phi0|Phi(n)> Phi0.
+   E(2) here is the Wigner form <Phi0|H|Q Phi1>; mpslcc_energy's E2 is the
+   Hylleraas value (they agree at the exact first-order state).  Writes
+   min(2N+2, max_terms) values to E and 2N+2 to *n_terms.  E_STATE without
+   E0 and Phi1. */
+mpslcc_status mpslcc_energy_series(mpslcc_ctx* ctx, double* E, int max_terms, int* n_terms);
 
 /* Local dimension of the two-site vector at position site (0..n_orb-2) for
    operator op (output dimension for transition ops is the Phi1 space; *n_in
@@ -248,7 +278,7 @@ mpslcc_status mpslcc_apply_heff(mpslcc_ctx* ctx, int site, int op, const double*
 mpslcc_status mpslcc_apply_heff_device(mpslcc_ctx* ctx, int site, int op, const double* d_psi,
                                        double* d_sigma, long n_in, long n_out, int prec);
 
-/* Replace MPS `which` (0 = Phi0, 1 = Phi1) by caller data (checkpoint
+/* Replace MPS `which` (0 = Phi0, n = 1..8 = Phi(n)) by caller data (checkpoint
    restore and test input).  bond_nsec[b] (b = 0..n_sites) sector counts;
    bond_qn: for every bond, 2*nsec ints (N, 2S_z) ascending; bond_dim: dims.
    site_nblk[p] block counts; blk_desc: per block (ia, s, ib) as sector

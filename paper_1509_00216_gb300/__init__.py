@@ -28,7 +28,9 @@ FLAG_NOCONV, FLAG_INDEFINITE, FLAG_E2_POSITIVE, FLAG_J_ROSE = 1, 2, 4, 8
 
 EXPORTED = [
     "mpslcc_default_opts", "mpslcc_create", "mpslcc_destroy", "mpslcc_last_error", "mpslcc_build_mpo",
-    "mpslcc_set_spaces", "mpslcc_dmrg_reference", "mpslcc_lcc_sweep", "mpslcc_energy", "mpslcc_local_dim",
+    "mpslcc_set_spaces", "mpslcc_dmrg_reference", "mpslcc_lcc_sweep", "mpslcc_lcc_sweep_window", "mpslcc_energy",
+    "mpslcc_energy_series",
+    "mpslcc_local_dim",
     "mpslcc_apply_heff", "mpslcc_apply_heff_device", "mpslcc_load_mps", "mpslcc_export_mps",
     "mpslcc_mpo_bond_dims", "mpslcc_export_mpo_site", "mpslcc_get_stats", "mpslcc_reset_stats",
     "mpslcc_debug_tc_gemm", "mpslcc_tc_gemm_noalloc", "mpslcc_tc_gemm_noalloc_scratch_bytes",
@@ -86,7 +88,9 @@ def _load():
         "mpslcc_set_spaces": (C.c_int, [vp, C.c_int, C.c_int]),
         "mpslcc_dmrg_reference": (C.c_int, [vp, C.c_int, C.c_int, dp]),
         "mpslcc_lcc_sweep": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, dp]),
+        "mpslcc_lcc_sweep_window": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp]),
         "mpslcc_energy": (C.c_int, [vp, C.POINTER(Energies)]),
+        "mpslcc_energy_series": (C.c_int, [vp, dp, C.c_int, ip]),
         "mpslcc_local_dim": (C.c_int, [vp, C.c_int, C.c_int, lp, lp]),
         "mpslcc_apply_heff": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, C.c_long, C.c_long, C.c_int]),
         "mpslcc_apply_heff_device": (C.c_int, [vp, C.c_int, C.c_int, vp, vp, C.c_long, C.c_long, C.c_int]),
@@ -242,6 +246,22 @@ class Context:
         e = C.c_double()
         self._check(lib().mpslcc_lcc_sweep(self.h, M1, order, n_sweeps, C.byref(e)), soft_noconv=True)
         return e.value
+
+    def lcc_window(self, M1, first, count, direction=1, order=1):
+        """Two-site steps over positions first, first + direction, ... (see
+        mpslcc_lcc_sweep_window); returns the last local Hylleraas value."""
+        e = C.c_double()
+        self._check(lib().mpslcc_lcc_sweep_window(self.h, M1, order, first, count, direction, C.byref(e)),
+                    soft_noconv=True)
+        return e.value
+
+    def energy_series(self):
+        """E(0), E(1), ..., E(2N+1) of the wavefunctions present (Eq. 2)."""
+        n = C.c_int()
+        self._check(lib().mpslcc_energy_series(self.h, None, 0, C.byref(n)))
+        out = np.zeros(n.value)
+        self._check(lib().mpslcc_energy_series(self.h, _dptr(out), n.value, C.byref(n)))
+        return out
 
     def energy(self):
         e = Energies()

@@ -56,6 +56,8 @@ void reset_families(Ctx& c) {
     F->R.clear();
     F->bra = F->ket = nullptr;
   }
+  c.ofam.clear();
+  c.series_valid = false;
 }
 
 void build_partition_mpos(Ctx& c) {
@@ -205,6 +207,7 @@ mpslcc_status mpslcc_build_mpo(mpslcc_ctx* ctx, const double* h, const double* V
     reset_families(c);
     c.phi0 = MPS();
     c.phi1 = MPS();
+    c.phin.clear();
     c.have_E0 = c.have_E2 = c.e3_valid = false;
     c.k = k;
     c.n_elec = n_elec;
@@ -234,6 +237,7 @@ mpslcc_status mpslcc_set_spaces(mpslcc_ctx* ctx, int n_core, int n_active) {
     reset_families(c);
     c.phi0 = MPS();
     c.phi1 = MPS();
+    c.phin.clear();
     c.have_E0 = c.have_E2 = c.e3_valid = false;
     c.n_core = n_core;
     c.n_active = n_active;
@@ -255,6 +259,7 @@ mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, doubl
     } else {
       reset_families(c);
       c.phi1 = MPS();
+      c.phin.clear();
       c.have_E2 = c.e3_valid = false;
       E = dmrg_reference(c, M0, n_sweeps);
     }
@@ -266,12 +271,40 @@ mpslcc_status mpslcc_lcc_sweep(mpslcc_ctx* ctx, int M1, int order, int n_sweeps,
   if (ctx) ctx->c.cf.reset();
   return noconv_status(ctx, guard(ctx, [&](Ctx& c) {
     need_device(c);
-    MPSLCC_REQUIRE(order == 1, ST_ARG, "only first order (order = 1) is implemented");
+    MPSLCC_REQUIRE(order >= 1 && order <= Ctx::MAX_ORDER, ST_ARG, "order must be in [1, 8]");
     MPSLCC_REQUIRE(M1 >= 1 && n_sweeps >= 1, ST_ARG, "M1 and n_sweeps must be positive");
     cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
-    double E2 = lcc_sweeps(c, M1, n_sweeps);
+    double E2 = lcc_sweeps(c, M1, n_sweeps, order);
     if (E2_out) *E2_out = E2;
   }));
+}
+
+mpslcc_status mpslcc_lcc_sweep_window(mpslcc_ctx* ctx, int M1, int order, int first, int count, int dir,
+                                      double* J_out) {
+  if (ctx) ctx->c.cf.reset();
+  return noconv_status(ctx, guard(ctx, [&](Ctx& c) {
+    need_device(c);
+    MPSLCC_REQUIRE(order >= 1 && order <= Ctx::MAX_ORDER, ST_ARG, "order must be in [1, 8]");
+    MPSLCC_REQUIRE(M1 >= 1, ST_ARG, "M1 must be positive");
+    cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
+    double J = lcc_window(c, M1, first, count, dir, order);
+    if (J_out) *J_out = J;
+  }));
+}
+
+mpslcc_status mpslcc_energy_series(mpslcc_ctx* ctx, double* E, int max_terms, int* n_terms) {
+  return guard(ctx, [&](Ctx& c) {
+    MPSLCC_REQUIRE(c.have_E0 && c.phi1.present, ST_STATE, "the energy series needs E0 and Phi1");
+    MPSLCC_REQUIRE(max_terms >= 0 && (E || max_terms == 0), ST_ARG, "bad output buffer");
+    if (!c.series_valid) {
+      need_device(c);
+      cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
+      compute_series(c);
+    }
+    const int n = (int)c.Eseries.size();
+    for (int i = 0; i < std::min(n, max_terms); ++i) E[i] = c.Eseries[i];
+    if (n_terms) *n_terms = n;
+  });
 }
 
 mpslcc_status mpslcc_energy(mpslcc_ctx* ctx, mpslcc_energies* out) {
@@ -370,7 +403,7 @@ mpslcc_status mpslcc_load_mps(mpslcc_ctx* ctx, int which, int n_sites, const int
   return guard(ctx, [&](Ctx& c) {
     need_device(c);
     cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
-    MPSLCC_REQUIRE(which == 0 || which == 1, ST_ARG, "which must be 0 or 1");
+    MPSLCC_REQUIRE(which >= 0 && which <= Ctx::MAX_ORDER, ST_ARG, "which must be in [0, 8]");
     MPSLCC_REQUIRE(c.have_mpo && n_sites == c.k, ST_ARG, "n_sites must equal n_orb");
     MPSLCC_REQUIRE(bond_nsec && bond_qn && bond_dim && site_nblk && blk_desc && data, ST_ARG, "null input");
     int k = n_sites;
@@ -401,7 +434,7 @@ mpslcc_status mpslcc_load_mps(mpslcc_ctx* ctx, int which, int n_sites, const int
     long pos = 0;
     int bi = 0;
     for (int p = 0; p < k; ++p) {
-      std::vector<int> seen(4, which == 1 ? 1 : 0);
+      std::vector<int> seen(4, which >= 1 ? 1 : 0);
       for (int t = 0; t < site_nblk[p]; ++t) {
         int ia = blk_desc[3 * bi], s = blk_desc[3 * bi + 1], ib = blk_desc[3 * bi + 2];
         ++bi;
@@ -445,16 +478,17 @@ mpslcc_status mpslcc_load_mps(mpslcc_ctx* ctx, int which, int n_sites, const int
       c.phi0 = std::move(m);
       c.have_E0 = false;
     } else {
-      c.phi1 = std::move(m);
+      *c.phi_of(which) = std::move(m);
     }
     c.have_E2 = c.e3_valid = c.e_valid = false;
+    c.series_valid = false;
   });
 }
 
 mpslcc_status mpslcc_export_mps(mpslcc_ctx* ctx, int which, int* meta, long* n_int, double* data, long* n_data) {
   return guard(ctx, [&](Ctx& c) {
-    MPSLCC_REQUIRE(which == 0 || which == 1, ST_ARG, "which must be 0 or 1");
-    MPS& m = which == 0 ? c.phi0 : c.phi1;
+    MPSLCC_REQUIRE(which >= 0 && which <= Ctx::MAX_ORDER, ST_ARG, "which must be in [0, 8]");
+    MPS& m = *c.phi_of(which);
     MPSLCC_REQUIRE(m.present, ST_STATE, "MPS not present");
     int k = m.k;
     std::vector<int> nsec, qn, dims, nblk, desc;

@@ -262,6 +262,36 @@ struct Ctx {
   Family u11;   // <Phi1|U|Phi1>
   Family h11;   // <Phi1|H|Phi1>
 
+  // higher orders (Eq. 1 for n >= 2): Phi(n) and, per order, the families of
+  // its sweeps: <Phi(n)|H0|Phi(n)>, <Phi(n)|U|Phi(n-1)>, <Phi(n)|Phi0> and
+  // <Phi(n)|Phi(j)> for j = 1 .. n-2
+  static constexpr int MAX_ORDER = 8;
+  struct OrderFamilies {
+    Family a, t, s0;
+    std::vector<Family> s;   // index j (1 .. n-2)
+  };
+  std::vector<std::unique_ptr<MPS>> phin;              // index n >= 2
+  std::vector<std::unique_ptr<OrderFamilies>> ofam;     // index n >= 2
+  std::vector<double> Eseries;                          // E(0 .. 2N+1), Eq. 2
+  bool series_valid = false;
+  MPS* phi_of(int n) {
+    if (n == 0) return &phi0;
+    if (n == 1) return &phi1;
+    if ((int)phin.size() <= n) phin.resize(n + 1);
+    if (!phin[n]) phin[n].reset(new MPS());
+    return phin[n].get();
+  }
+  int highest_order() {
+    int n = phi1.present ? 1 : 0;
+    while (n >= 1 && n + 1 < (int)phin.size() && phin[n + 1] && phin[n + 1]->present) ++n;
+    return n;
+  }
+  void clear_orders_above(int n) {   // Phi(m) for m > n and their families
+    for (int m = std::max(n + 1, 2); m < (int)phin.size(); ++m) phin[m].reset();
+    for (int m = std::max(n + 1, 2); m < (int)ofam.size(); ++m) ofam[m].reset();
+    series_valid = false;
+  }
+
   // scratch
   DBuf red, red_out, gtask, ctask;
   DBuf eig_work, eig_w, eig_info;
@@ -326,7 +356,9 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
 // sweeps (sweep.cpp)
 void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed);
 double dmrg_reference(Ctx& c, int M0, int n_sweeps);
-double lcc_sweeps(Ctx& c, int M1, int n_sweeps);
+double lcc_sweeps(Ctx& c, int M1, int n_sweeps, int order = 1);
+double lcc_window(Ctx& c, int M1, int first, int count, int dir, int order = 1);
+void compute_series(Ctx& c);
 void compute_e3(Ctx& c);
 void compute_energies(Ctx& c);
 double reference_energy_fp64(Ctx& c);

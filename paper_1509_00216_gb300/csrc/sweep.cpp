@@ -837,29 +837,56 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
   return E;
 }
 
-// One local step of the first-order solve at two-site position l (Eq. 1
-// with n = 1, projector form): b = -Q_loc (P1^T H Phi0 - E0 v) with
-// v = P1^T Phi0 and Q_loc = 1 - v v^T / |v|^2, then Q_loc (H0_eff - E0) Q_loc
-// x = b from the current two-site state of Phi1.  Products in `prec` (the
-// right-hand side in `rprec`); xb receives x.  Returns the local Hylleraas
-// value J = x.Ax - 2 x.b.
-double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, int prec, int rprec, DBuf& xb,
-                 int* its_out, bool* indef_out) {
-  long n = P11.nk, n0 = P10.nk;
+// A term of the local right-hand side: coef * (P^T ket - sref * v), the
+// local projection (plan P, input the ket's two-site tensor) of coef * Q ket
+// with v = P^T Phi0 and sref = <Phi0|ket>.
+struct RhsTerm {
+  SigmaPlan* P;
+  MPS* ket;
+  double coef, sref;
+};
+
+// One local step of the order-n solve at two-site position l (Eq. 1 in
+// projector form): b = -(P^T O Phi(n-1) - o v) + sum_k E(k) (P^T Phi(n-k) -
+// s_k v), with O = H and o = E0 for n = 1 (b = -Q H Phi0), O = U and
+// o = <Phi0|U|Phi(n-1)> for n >= 2; v = P^T Phi0 (plan PS) and
+// Q_loc = 1 - v v^T / |v|^2 projects b; then Q_loc (H0_eff - E0) Q_loc x = b
+// from the current two-site state of the target MPS.  Products in `prec`
+// (the right-hand side in `rprec`); xb receives x.  Returns the local
+// Hylleraas value J = x.Ax - 2 x.b.
+double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket, double tscalar, SigmaPlan& PS,
+                 const std::vector<RhsTerm>& extra, int l, int prec, int rprec, DBuf& xb, int* its_out,
+                 bool* indef_out) {
+  long n = P11.nk, n0 = P10.nk, ns = PS.nk;
   xb.alloc(&c, std::max(n, 1L) * sizeof(double));
-  DBuf bb, ub, sb, dg, p0;
+  DBuf bb, ub, sb, dg, p0, pt;
   std::unique_ptr<StageTimer> trhs(new StageTimer(c, &c.st.t_rhs));
   bb.alloc(&c, std::max(n, 1L) * sizeof(double));
   ub.alloc(&c, std::max(n, 1L) * sizeof(double));
   sb.alloc(&c, std::max(n, 1L) * sizeof(double));
   dg.alloc(&c, std::max(n, 1L) * sizeof(double));
-  p0.alloc(&c, std::max(n0, 1L) * sizeof(double));
+  p0.alloc(&c, std::max(ns, 1L) * sizeof(double));
   form_two_site(c, c.phi0, l, p0.d());
-  sigma_apply(c, P10, p0.d(), sb.d(), rprec);   // P1^T H Phi0
-  sigma_apply(c, PS, p0.d(), ub.d(), rprec);    // v = P1^T Phi0
-  // b = -(P1^T H Phi0 - E0 v), then project out v
+  sigma_apply(c, PS, p0.d(), ub.d(), rprec);    // v = P^T Phi0
+  const double* tin = p0.d();
+  if (&tket != &c.phi0) {
+    pt.alloc(&c, std::max(n0, 1L) * sizeof(double));
+    form_two_site(c, tket, l, pt.d());
+    tin = pt.d();
+  }
+  sigma_apply(c, P10, tin, sb.d(), rprec);      // P^T O Phi(n-1)
+  // b = -(P^T O Phi(n-1) - o v)
   copyv(c, bb.d(), ub.d(), n);
-  launch_axpby(n, -1.0, sb.d(), c.E0, bb.d(), c.s());
+  launch_axpby(n, -1.0, sb.d(), tscalar, bb.d(), c.s());
+  for (const RhsTerm& t : extra) {              // + E(k) (P^T Phi(n-k) - s v)
+    DBuf pk, yk;
+    pk.alloc(&c, std::max(t.P->nk, 1L) * sizeof(double));
+    yk.alloc(&c, std::max(n, 1L) * sizeof(double));
+    form_two_site(c, *t.ket, l, pk.d());
+    sigma_apply(c, *t.P, pk.d(), yk.d(), rprec);
+    launch_axpy(n, t.coef, yk.d(), bb.d(), c.s());
+    launch_axpy(n, -t.coef * t.sref, ub.d(), bb.d(), c.s());
+  }
   double vn = std::sqrt(std::max(0.0, dev_dot(c, ub.d(), ub.d(), n)));
   const double* u = nullptr;
   if (vn > 1e-10) {
@@ -867,7 +894,7 @@ double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, i
     u = ub.d();
   }
   project(c, u, bb.d(), n);
-  form_two_site(c, c.phi1, l, xb.d());
+  form_two_site(c, target, l, xb.d());
   sigma_diag(c, P11, dg.d());
   trhs.reset();
   std::unique_ptr<StageTimer> tsol(new StageTimer(c, &c.st.t_solve));
@@ -942,32 +969,166 @@ double lcc_local(Ctx& c, SigmaPlan& P11, SigmaPlan& P10, SigmaPlan& PS, int l, i
   return J;
 }
 
-double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
-  int k = c.k;
-  MPSLCC_REQUIRE(c.phi0.present && c.have_E0, ST_STATE, "lcc_sweep needs a reference (dmrg_reference)");
-  if (!c.phi1.present) {
-    init_random_mps(c, c.phi1, std::min(M1, 16), false, c.opts.seed + 1);
-    bind(c, c.f11, &c.phi1, MPO_H0, &c.phi1);
-    bind(c, c.f10, &c.phi1, MPO_H, &c.phi0);
-    bind(c, c.s10, &c.phi1, MPO_ID, &c.phi0);
-  }
-  // a loaded Phi1 (or Phi0) leaves the families unbound
-  if (!c.f11.bra) bind(c, c.f11, &c.phi1, MPO_H0, &c.phi1);
-  if (!c.f10.bra) bind(c, c.f10, &c.phi1, MPO_H, &c.phi0);
-  if (!c.s10.bra) bind(c, c.s10, &c.phi1, MPO_ID, &c.phi0);
-  c.e3_valid = false;
-  c.e_valid = false;
-  c.u11.L.clear();
-  c.h11.L.clear();
-  c.cf.reset();
+namespace {
+
+double expect_norm(Ctx& c, MPS* bra, int mpo, MPS* ket);
+
+// Families, precision and right-hand-side data of the sweeps of one order
+// (Eq. 1: n = 1 is the first-order wavefunction, n >= 2 the higher orders);
+// shared by full sweeps and windows of positions.
+struct LccRun {
+  Ctx& c;
+  int M1, order, prec, rprec;
+  MPS* target;
+  MPS* tket;                  // ket of the transition term: Phi0 (n = 1) or Phi(n-1)
+  double tscalar;             // E0 (n = 1) or <Phi0|U|Phi(n-1)>
+  Family *fa, *ft, *fs0;
+  std::vector<Family*> fx;    // <Phi(n)|Phi(n-k)>, k = 2 .. n-1
+  std::vector<MPS*> xket;
+  std::vector<double> xcoef, xsref;
   double J_prev = HUGE_VAL;
-  int prec = c.opts.prec;
-  const bool mixed = prec != MPSLCC_FP64;
-  GemmPrec gp(c, mixed ? MPSLCC_BF16X3 : MPSLCC_FP64);
-  // right-hand side and residuals: BF16X6 products in mixed precision
-  const int rprec = mixed ? MPSLCC_BF16X6 : MPSLCC_FP64;
-  double J = 0, E2 = 0;
-  FusedAhead ahead[3];
+  std::vector<FusedAhead> ahead;
+
+  LccRun(Ctx& c_, int M1_, int order_) : c(c_), M1(M1_), order(order_) {
+    MPSLCC_REQUIRE(c.phi0.present && c.have_E0, ST_STATE, "lcc_sweep needs a reference (dmrg_reference)");
+    MPSLCC_REQUIRE(order >= 1 && order <= Ctx::MAX_ORDER, ST_ARG, "order out of range");
+    if (order >= 2)
+      MPSLCC_REQUIRE(c.phi_of(order - 1)->present, ST_STATE,
+                     "order n >= 2 needs the wavefunction of order n-1 (sweep or load it first)");
+    target = c.phi_of(order);
+    if (order == 1) {
+      if (!c.phi1.present) {
+        init_random_mps(c, c.phi1, std::min(M1, 16), false, c.opts.seed + 1);
+        c.f11.bra = c.f10.bra = c.s10.bra = nullptr;
+      }
+      // a loaded Phi1 (or Phi0) leaves the families unbound
+      if (!c.f11.bra) bind(c, c.f11, &c.phi1, MPO_H0, &c.phi1);
+      if (!c.f10.bra) bind(c, c.f10, &c.phi1, MPO_H, &c.phi0);
+      if (!c.s10.bra) bind(c, c.s10, &c.phi1, MPO_ID, &c.phi0);
+      fa = &c.f11, ft = &c.f10, fs0 = &c.s10;
+      tket = &c.phi0;
+      tscalar = c.E0;
+      c.u11.L.clear();
+      c.h11.L.clear();
+    } else {
+      if (!target->present) init_random_mps(c, *target, std::min(M1, 16), false, c.opts.seed + (unsigned)order);
+      if ((int)c.ofam.size() <= order) c.ofam.resize(order + 1);
+      auto& of = c.ofam[order];
+      if (!of || !of->a.bra) {
+        of.reset(new Ctx::OrderFamilies());
+        bind(c, of->a, target, MPO_H0, target);
+        bind(c, of->t, target, MPO_U, c.phi_of(order - 1));
+        bind(c, of->s0, target, MPO_ID, &c.phi0);
+        of->s.resize(order - 1);
+        for (int j = 1; j <= order - 2; ++j) bind(c, of->s[j], target, MPO_ID, c.phi_of(j));
+      }
+      fa = &of->a, ft = &of->t, fs0 = &of->s0;
+      tket = c.phi_of(order - 1);
+      // FP64 scalars of the right-hand side: the Eq. 2 energies of the lower
+      // orders, <Phi0|U|Phi(n-1)> and the reference overlaps <Phi0|Phi(j)>
+      if (!c.series_valid || (int)c.Eseries.size() < 2 * (order - 1) + 2) compute_series(c);
+      tscalar = expect_norm(c, &c.phi0, MPO_U, tket);
+      for (int k = 2; k <= order - 1; ++k) {
+        const int j = order - k;
+        fx.push_back(&of->s[j]);
+        xket.push_back(c.phi_of(j));
+        xcoef.push_back(c.Eseries[k]);
+        xsref.push_back(expect_norm(c, &c.phi0, MPO_ID, c.phi_of(j)));
+      }
+    }
+    // the wavefunctions of higher orders depend on this one
+    c.clear_orders_above(order);
+    c.series_valid = false;
+    c.e3_valid = false;
+    c.e_valid = false;
+    c.cf.reset();
+    prec = c.opts.prec;
+    // right-hand side and residuals: BF16X6 products in mixed precision
+    rprec = prec != MPSLCC_FP64 ? MPSLCC_BF16X6 : MPSLCC_FP64;
+    ahead.resize(3 + fx.size());
+  }
+
+  std::vector<Family*> families() {
+    std::vector<Family*> f{fa, ft, fs0};
+    f.insert(f.end(), fx.begin(), fx.end());
+    return f;
+  }
+
+  // One two-site step at position l moving right (or left): local linear
+  // solve, truncation to M1, environment renormalisation.  `next` >= 0 is the
+  // position that follows (its fused operators are built during truncation).
+  double step(int l, bool right, int next, int sw) {
+    std::vector<Family*> fams = families();
+    std::vector<std::unique_ptr<SigmaPlan>> plans;
+    {
+      StageTimer tm(c, &c.st.t_plan);
+      for (size_t i = 0; i < fams.size(); ++i) {
+        plans.emplace_back(new SigmaPlan());
+        make_sigma_plan(c, *fams[i], l, *plans.back(), &ahead[i]);
+      }
+      if (prec != MPSLCC_FP64) tc_prepare(c, *plans[0], MPSLCC_BF16X3);
+    }
+    std::vector<RhsTerm> extra;
+    for (size_t i = 0; i < fx.size(); ++i) extra.push_back({plans[3 + i].get(), xket[i], xcoef[i], xsref[i]});
+    DBuf xb;
+    int its = 0;
+    bool indef = false;
+    const double J = lcc_local(c, *target, *plans[0], *plans[1], *tket, tscalar, *plans[2], extra, l, prec, rprec, xb,
+                               &its, &indef);
+    // within a sweep the local minima do not rise, up to truncation effects
+    if (J > J_prev + 1e-6 * std::max(1e-12, std::fabs(J_prev))) c.cf.j_rise++;
+    J_prev = J;
+    double disc;
+    {
+      StageTimer tm(c, &c.st.t_trunc);
+      // the next position's fused operators on the side this truncation
+      // leaves alone are built while the eigensolvers run
+      std::function<void()> nextf;
+      FusedAhead* ah = ahead.data();
+      if (next >= 0)
+        nextf = [this, ah, fams, next, right]() {
+          for (size_t fi = 0; fi < fams.size(); ++fi) build_fused_ahead(c, *fams[fi], next, right, ah[fi]);
+        };
+      disc = truncate(c, *target, l, xb.d(), M1, right, nextf);
+    }
+    c.max_disc = std::max(c.max_disc, disc);
+    for (Family* F : fams) {
+      invalidate_site(*F, l);
+      invalidate_site(*F, l + 1);
+    }
+    StageTimer tenv(c, &c.st.t_env);
+    for (size_t i = 0; i < fams.size(); ++i) {
+      if (right) env_update_left(c, *fams[i], l, plans[i]->lf);
+      else env_update_right(c, *fams[i], l + 1, plans[i]->rf);
+    }
+    if (c.opts.verbose)
+      fprintf(stderr, "[lcc%d] sweep %d %s l=%d n=%ld its=%d%s J=%.12f disc=%.2e\n", order, sw, right ? "R" : "L", l,
+              plans[0]->nk, its, indef ? " (minres)" : "", J, disc);
+    return J;
+  }
+
+  void finish(double J) {
+    if (order == 1) {
+      c.J = J;
+      c.E2 = J;
+      c.have_E2 = true;
+    }
+    c.st.n_noconv += c.cf.noconv;
+    c.st.n_indefinite += c.cf.indefinite;
+    c.st.n_j_rise += c.cf.j_rise;
+    c.st.max_rel_residual = c.cf.max_rel_residual;
+    c.flags = (c.cf.noconv ? MPSLCC_FLAG_NOCONV : 0) | (c.cf.indefinite ? MPSLCC_FLAG_INDEFINITE : 0) |
+              (c.cf.j_rise ? MPSLCC_FLAG_J_ROSE : 0);
+  }
+};
+
+}  // namespace
+
+double lcc_sweeps(Ctx& c, int M1, int n_sweeps, int order) {
+  const int k = c.k;
+  LccRun run(c, M1, order);
+  GemmPrec gp(c, run.prec != MPSLCC_FP64 ? MPSLCC_BF16X3 : MPSLCC_FP64);
+  double J = 0;
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
@@ -976,57 +1137,11 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
     long long n_sig0 = c.st.sigma_calls, n_k0 = c.st.kernel_launches;
     cudaEventRecord(t0, c.s());
     for (int dir = 0; dir < 2; ++dir) {
-      bool right = dir == 0;
+      const bool right = dir == 0;
       for (int step = 0; step <= k - 2; ++step) {
-        int l = right ? step : k - 2 - step;
-        SigmaPlan P11, P10, PS;
-        {
-          StageTimer tm(c, &c.st.t_plan);
-          make_sigma_plan(c, c.f11, l, P11, &ahead[0]);
-          make_sigma_plan(c, c.f10, l, P10, &ahead[1]);
-          make_sigma_plan(c, c.s10, l, PS, &ahead[2]);
-          if (prec != MPSLCC_FP64) tc_prepare(c, P11, MPSLCC_BF16X3);
-        }
-        DBuf xb;
-        int its = 0;
-        bool indef = false;
-        J = lcc_local(c, P11, P10, PS, l, prec, rprec, xb, &its, &indef);
-        E2 = J;
-        // within a sweep the local minima do not rise, up to truncation effects
-        if (J > J_prev + 1e-6 * std::max(1e-12, std::fabs(J_prev))) c.cf.j_rise++;
-        J_prev = J;
-        double disc;
-        {
-          StageTimer tm(c, &c.st.t_trunc);
-          // the next position's fused operator on the side this truncation
-          // leaves alone is built while the eigensolvers run
-          const int ln = right ? l + 1 : l - 1;
-          std::function<void()> next;
-          if (ln >= 0 && ln <= k - 2)
-            next = [&c, &ahead, ln, right]() {
-              Family* fams[3] = {&c.f11, &c.f10, &c.s10};
-              for (int fi = 0; fi < 3; ++fi) build_fused_ahead(c, *fams[fi], ln, right, ahead[fi]);
-            };
-          disc = truncate(c, c.phi1, l, xb.d(), M1, right, next);
-        }
-        c.max_disc = std::max(c.max_disc, disc);
-        for (Family* F : {&c.f11, &c.f10, &c.s10}) {
-          invalidate_site(*F, l);
-          invalidate_site(*F, l + 1);
-        }
-        StageTimer tenv(c, &c.st.t_env);
-        if (right) {
-          env_update_left(c, c.f11, l, P11.lf);
-          env_update_left(c, c.f10, l, P10.lf);
-          env_update_left(c, c.s10, l, PS.lf);
-        } else {
-          env_update_right(c, c.f11, l + 1, P11.rf);
-          env_update_right(c, c.f10, l + 1, P10.rf);
-          env_update_right(c, c.s10, l + 1, PS.rf);
-        }
-        if (c.opts.verbose)
-          fprintf(stderr, "[lcc] sweep %d %s l=%d n=%ld its=%d%s J=%.12f disc=%.2e\n", sw, right ? "R" : "L", l, P11.nk,
-                  its, indef ? " (minres)" : "", J, disc);
+        const int l = right ? step : k - 2 - step;
+        const int ln = right ? l + 1 : l - 1;
+        J = run.step(l, right, (ln >= 0 && ln <= k - 2) ? ln : -1, sw);
       }
     }
     cudaEventRecord(t1, c.s());
@@ -1038,20 +1153,35 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps) {
     c.st.last_sweep_sigma_flops = c.st.sigma_flops - f_sig0;
     c.st.last_sweep_sigma_calls = c.st.sigma_calls - n_sig0;
     c.st.last_sweep_kernel_launches = c.st.kernel_launches - n_k0;
-    c.sweeps_done++;
+    if (order == 1) c.sweeps_done++;
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
-  c.J = J;
-  c.E2 = E2;
-  c.have_E2 = true;
-  c.st.n_noconv += c.cf.noconv;
-  c.st.n_indefinite += c.cf.indefinite;
-  c.st.n_j_rise += c.cf.j_rise;
-  c.st.max_rel_residual = c.cf.max_rel_residual;
-  c.flags = (c.cf.noconv ? MPSLCC_FLAG_NOCONV : 0) | (c.cf.indefinite ? MPSLCC_FLAG_INDEFINITE : 0) |
-            (c.cf.j_rise ? MPSLCC_FLAG_J_ROSE : 0);
-  return E2;
+  run.finish(J);
+  return J;
+}
+
+// A window of a half sweep: `count` two-site steps from position `first`
+// towards increasing (dir > 0) or decreasing positions.  The local problem
+// P^T (H0 - E0) P is the LCC matrix only when the first position is the
+// orthogonality centre of Phi1 (sites left of it left-orthonormal, right of
+// it right-orthonormal), as it is after a full sweep (position 0) or after
+// a window that ended next to it.
+double lcc_window(Ctx& c, int M1, int first, int count, int dir, int order) {
+  const int k = c.k;
+  MPSLCC_REQUIRE(count >= 1 && (dir == 1 || dir == -1), ST_ARG, "window needs count >= 1 and dir = +1 or -1");
+  const int last = first + dir * (count - 1);
+  MPSLCC_REQUIRE(first >= 0 && first <= k - 2 && last >= 0 && last <= k - 2, ST_ARG,
+                 "window positions must lie in [0, n_orb - 2]");
+  LccRun run(c, M1, order);
+  GemmPrec gp(c, run.prec != MPSLCC_FP64 ? MPSLCC_BF16X3 : MPSLCC_FP64);
+  double J = 0;
+  for (int i = 0; i < count; ++i) {
+    const int l = first + dir * i;
+    J = run.step(l, dir > 0, i + 1 < count ? l + dir : -1, 0);
+  }
+  run.finish(J);
+  return J;
 }
 
 // <bra|O|ket> in FP64 from freshly built FP64 environments, contracted at
@@ -1111,5 +1241,63 @@ void compute_energies(Ctx& c) {
 }
 
 void compute_e3(Ctx& c) { compute_energies(c); }
+
+namespace {
+// <bra|O|ket> with the reference normalised wherever it appears
+double expect_norm(Ctx& c, MPS* bra, int mpo, MPS* ket) {
+  double v = expect_fp64(c, bra, mpo, ket);
+  if (bra == &c.phi0 || ket == &c.phi0) {
+    const double n00 = expect_fp64(c, &c.phi0, MPO_ID, &c.phi0);
+    MPSLCC_REQUIRE(n00 > 0, ST_STATE, "reference has zero norm");
+    v /= (bra == &c.phi0 && ket == &c.phi0) ? n00 : std::sqrt(n00);
+  }
+  return v;
+}
+}  // namespace
+
+// Eq. 2 (Wigner 2n+1 rule) for the wavefunctions Phi(1..N) present, each
+// taken as Q Phi(n) = Phi(n) - <Phi0|Phi(n)> Phi0 (Phi0 normalised): between
+// Q-space states the perturbation of the projector partition is U, so
+//   E(2n)   = <Q Phi(n-1)|U|Q Phi(n)> - sum_{k=1..n} sum_{j=1..n-1} E(2n-k-j) <Q Phi(k)|Q Phi(j)>,
+//   E(2n+1) = <Q Phi(n)|U|Q Phi(n)>   - sum_{k=1..n} sum_{j=1..n}   E(2n+1-k-j) <Q Phi(k)|Q Phi(j)>,
+// with E(0) = <Phi0|H|Phi0>, E(1) = <Phi0|U|Phi0> (zero: U has no block in the
+// reference class) and, for n = 1, the first term <Phi0|H|Q Phi1>.
+void compute_series(Ctx& c) {
+  const int N = c.highest_order();
+  MPSLCC_REQUIRE(N >= 1 && c.have_E0, ST_STATE, "the energy series needs E0 and Phi1");
+  std::vector<MPS*> ph(N + 1);
+  for (int n = 0; n <= N; ++n) ph[n] = c.phi_of(n);
+  const double n00 = expect_fp64(c, ph[0], MPO_ID, ph[0]);
+  MPSLCC_REQUIRE(n00 > 0, ST_STATE, "reference has zero norm");
+  const double r0 = 1.0 / std::sqrt(n00);
+  std::vector<std::vector<double>> S(N + 1, std::vector<double>(N + 1)), Uu = S;
+  for (int a = 0; a <= N; ++a)
+    for (int b = a; b <= N; ++b) {
+      const double f = (a == 0 ? r0 : 1.0) * (b == 0 ? r0 : 1.0);
+      S[a][b] = S[b][a] = f * expect_fp64(c, ph[a], MPO_ID, ph[b]);
+      Uu[a][b] = Uu[b][a] = f * expect_fp64(c, ph[a], MPO_U, ph[b]);
+    }
+  const double h00 = expect_fp64(c, ph[0], MPO_H, ph[0]) / n00;
+  const double h01 = r0 * expect_fp64(c, ph[0], MPO_H, ph[1]);
+  std::vector<double> s(N + 1, 0.0);
+  for (int a = 1; a <= N; ++a) s[a] = S[a][0];
+  auto qS = [&](int a, int b) { return S[a][b] - s[a] * s[b]; };
+  auto qU = [&](int a, int b) { return Uu[a][b] - s[a] * Uu[0][b] - s[b] * Uu[a][0] + s[a] * s[b] * Uu[0][0]; };
+  std::vector<double> E(2 * N + 2, 0.0);
+  E[0] = h00;
+  E[1] = Uu[0][0];
+  for (int n = 1; n <= N; ++n) {
+    double e = n == 1 ? h01 - s[1] * h00 : qU(n - 1, n);
+    for (int k = 1; k <= n; ++k)
+      for (int j = 1; j <= n - 1; ++j) e -= E[2 * n - k - j] * qS(k, j);
+    E[2 * n] = e;
+    e = qU(n, n);
+    for (int k = 1; k <= n; ++k)
+      for (int j = 1; j <= n; ++j) e -= E[2 * n + 1 - k - j] * qS(k, j);
+    E[2 * n + 1] = e;
+  }
+  c.Eseries = E;
+  c.series_valid = true;
+}
 
 }  // namespace mpslcc

@@ -123,3 +123,31 @@ def test_loaded_states_with_reference_admixture(mpslcc, chain):
         o = _check_states(ctx, chain, e)
     assert abs(o["overlap01"] - 1.0) < 1e-10
     assert abs(e["E2"]) < 1e-10 and abs(e["E3"]) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["FP64", "BF16X3"])
+def test_sweep_windows_reproduce_the_sweep_bit_for_bit(mpslcc, chain, prec):
+    """A full sweep run as two windows (positions 0..6 left to right, then
+    6..0 right to left) gives the same states and energies as mpslcc_lcc_sweep,
+    to the last bit: the split-K partial sums are added in a fixed order, so
+    two runs of the same work agree exactly."""
+    c = chain["c"]
+    res = []
+    for mode in ("sweep", "windows", "sweep"):
+        with mpslcc.Context(device=0, prec=getattr(mpslcc, prec), tol=1e-10) as ctx:
+            ctx.build_mpo(c["h"], c["V"], 8, 0)
+            ctx.set_spaces(c["n_core"], c["n_active"])
+            ctx.dmrg_reference(16, 2)
+            ctx.lcc_sweep(64, 1)
+            if mode == "sweep":
+                ctx.lcc_sweep(64, 1)
+            else:
+                ctx.lcc_window(64, 0, 7, 1)
+                ctx.lcc_window(64, 6, 7, -1)
+            e = ctx.energy()
+            p1 = ctx.export_mps(1)
+        res.append((e, np.concatenate([b.ravel() for s in p1["sites"] for _, b in sorted(s.items())])))
+    for e, v in res[1:]:
+        for key in ("E0", "E2", "E3"):
+            assert e[key] == res[0][0][key], (key, e[key], res[0][0][key])
+        assert np.array_equal(v, res[0][1])
