@@ -108,7 +108,12 @@ typedef struct {
   int tc_environments;   /* 1: the environments and fused operators that
                             mpslcc_apply_heff builds run on the tensor cores
                             as inside mixed-precision sweeps (three-piece
-                            BF16 split, about 2^-24 relative); 0: FP64     */
+                            BF16 split, about 2^-24 relative per product);
+                            0: FP64                                        */
+  int autotune;          /* tile-shape autotuner of the tensor-core sigma
+                            phases: 1 (default) tries N tiles of 256, 128 and
+                            64 rows on the first products of each position
+                            and keeps the fastest; 0 uses 256              */
 } mpslcc_opts;
 
 typedef struct {
@@ -180,10 +185,15 @@ typedef struct {
                                above the previous position's (1e-6 rel.)    */
   double max_rel_residual;  /* largest final relative residual |b - Ax|/|b|
                                of the local LCC solves of the last call      */
+  long long tune_trials;    /* autotuner trial launches                      */
+  long long tc_launches_n256; /* tensor-core sigma launches with N tiles of
+                                 at most 256 rows (chosen by the autotuner)  */
+  long long tc_launches_n128;
+  long long tc_launches_n64;
 } mpslcc_stats;
 
 /* Fill *opts with defaults (device 0, FP64, tol 1e-10, max_iter 200, auto
-   solver, subspace 24, refine 4, seed 7). */
+   solver, subspace 24, refine 4, seed 7, autotuner on). */
 void mpslcc_default_opts(mpslcc_opts* opts);
 
 /* Create / destroy a context.  Errors: E_ARG (NULL), E_CUDA (device). */

@@ -170,3 +170,51 @@ def to_vector(mps, dets: np.ndarray) -> np.ndarray:
         if pos < len(dets) and dets[pos] == m:
             out[pos] += v[0]
     return out
+
+
+# ----------------------------------------------------------------------------
+# one-site local problem (Implementation section: only the tensor of one site
+# is optimised at a time)
+# ----------------------------------------------------------------------------
+def local_layout1(mps, l: int):
+    """Entries (ia, a, s, ib, b) of the one-site local vector at site l, in
+    order: bond-(l+1) sectors q ascending (those reachable from bond l), each a
+    row-major block with rows = (s ascending, bond-l sector ascending, a) and
+    columns = the index b within sector q of bond l+1."""
+    bonds, masks = mps["bonds"], mps["masks"]
+    bl, br = bonds[l], bonds[l + 1]
+    entries = []
+    for ib, (n, z, db) in enumerate(br):
+        rows = []
+        for s in sorted(masks[l]):
+            for ia, (na, za, da) in enumerate(bl):
+                if (na + LOCAL_N[s], za + LOCAL_2SZ[s]) == (n, z):
+                    rows.append((s, ia, da))
+        for (s, ia, da) in rows:
+            for a in range(da):
+                for b in range(db):
+                    entries.append((ia, a, s, ib, b))
+    return entries
+
+
+def isometry1(mps, l: int, dets: np.ndarray) -> np.ndarray:
+    """Dense P [n_dets x n_local] of site l: P[(.., s_l, ..), (ia, a, s, ib, b)]
+    = L[config_left, a] R[b, config_right] delta(s_l, s), L / R the
+    contractions of sites < l and > l."""
+    entries = local_layout1(mps, l)
+    left = left_basis(mps, l)
+    right = right_basis(mps, l - 1)
+    byL, byR = {}, {}
+    for (m, ia, v) in left:
+        byL.setdefault(ia, []).append((m, v))
+    for (m, ib, v) in right:
+        byR.setdefault(ib, []).append((m, v))
+    P = np.zeros((len(dets), len(entries)))
+    for j, (ia, a, s, ib, b) in enumerate(entries):
+        for (mL, vL) in byL.get(ia, []):
+            for (mR, vR) in byR.get(ib, []):
+                full = mL | mR | _site_bits(l, s)
+                pos = np.searchsorted(dets, full)
+                if pos < len(dets) and dets[pos] == full:
+                    P[pos, j] += vL[a] * vR[b]
+    return P

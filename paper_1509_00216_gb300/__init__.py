@@ -45,7 +45,8 @@ class Opts(C.Structure):
                 ("max_iter", C.c_int), ("solver", C.c_int), ("davidson_max_subspace", C.c_int),
                 ("refine_steps", C.c_int), ("seed", C.c_ulonglong), ("verbose", C.c_int),
                 ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p),
-                ("init_guess", C.c_int), ("wait_timeout_s", C.c_double), ("tc_environments", C.c_int)]
+                ("init_guess", C.c_int), ("wait_timeout_s", C.c_double), ("tc_environments", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class Energies(C.Structure):
@@ -68,7 +69,9 @@ class Stats(C.Structure):
                 ("t_env", C.c_double), ("t_solve", C.c_double), ("t_rhs", C.c_double),
                 ("t_fuse_left", C.c_double), ("t_fuse_right", C.c_double), ("t_tc_prepare", C.c_double),
                 ("ahead_used", C.c_longlong), ("ahead_missed", C.c_longlong), ("n_noconv", C.c_longlong),
-                ("n_indefinite", C.c_longlong), ("n_j_rise", C.c_longlong), ("max_rel_residual", C.c_double)]
+                ("n_indefinite", C.c_longlong), ("n_j_rise", C.c_longlong), ("max_rel_residual", C.c_double),
+                ("tune_trials", C.c_longlong), ("tc_launches_n256", C.c_longlong), ("tc_launches_n128", C.c_longlong),
+                ("tc_launches_n64", C.c_longlong)]
 
 
 def _load():
@@ -156,7 +159,7 @@ class Context:
 
     def __init__(self, device=0, prec=FP64, tol=1e-10, max_iter=200, seed=7, verbose=0, refine_steps=4,
                  davidson_max_subspace=24, torch_memory=False, init_guess=0, wait_timeout_s=0.0, alloc=None,
-                 stream=None, tc_environments=False):
+                 stream=None, tc_environments=False, autotune=True):
         L = lib()
         o = Opts()
         L.mpslcc_default_opts(C.byref(o))
@@ -171,6 +174,7 @@ class Context:
         o.init_guess = init_guess
         o.wait_timeout_s = wait_timeout_s
         o.tc_environments = 1 if tc_environments else 0
+        o.autotune = 1 if autotune else 0
         if stream is not None:
             o.stream = C.c_void_p(stream)
         self._cb = None

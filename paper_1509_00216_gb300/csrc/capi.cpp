@@ -112,6 +112,7 @@ void mpslcc_default_opts(mpslcc_opts* o) {
   o->init_guess = 0;
   o->seed = 7;
   o->verbose = 0;
+  o->autotune = 1;
 }
 
 mpslcc_status mpslcc_create(mpslcc_ctx** out, const mpslcc_opts* opts) {
@@ -152,9 +153,13 @@ mpslcc_status mpslcc_destroy(mpslcc_ctx* ctx) {
   Ctx& c = ctx->c;
   if (!c.host_only) {
     cudaSetDevice(c.device);
+    // every member that owns device memory is released here, while the
+    // stream its frees are ordered on still exists
     reset_families(c);
     c.phi0 = MPS();
     c.phi1 = MPS();
+    c.phin.clear();
+    c.ofam.clear();
     for (auto& b : c.boxes) b.release();
     for (DBuf* b : {&c.red, &c.red_out, &c.gtask, &c.ctask, &c.eig_work, &c.eig_w, &c.eig_info, &c.scratch_a,
                     &c.scratch_b, &c.scratch_tc, &c.tc_conv_tasks, &c.tc_gemm_tasks, &c.tc_err})
@@ -611,6 +616,10 @@ mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out) {
     out->n_indefinite = c.st.n_indefinite;
     out->n_j_rise = c.st.n_j_rise;
     out->max_rel_residual = c.st.max_rel_residual;
+    out->tune_trials = c.st.tune_trials;
+    out->tc_launches_n256 = c.st.tc_cap_launches[0];
+    out->tc_launches_n128 = c.st.tc_cap_launches[1];
+    out->tc_launches_n64 = c.st.tc_cap_launches[2];
   });
 }
 

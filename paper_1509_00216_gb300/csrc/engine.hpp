@@ -205,6 +205,8 @@ struct Stats {
   long long ahead_used = 0, ahead_missed = 0;
   long long n_noconv = 0, n_indefinite = 0, n_j_rise = 0;
   double max_rel_residual = 0;
+  long long tune_trials = 0;
+  long long tc_cap_launches[3] = {0, 0, 0};   // sigma launches per N-tile cap 256 / 128 / 64
 };
 
 // Solver outcome counters of the current sweep call (reset per call).
@@ -305,6 +307,27 @@ struct Ctx {
   // precision of the per-site FP64 GEMM tasks (fusion, renormalisation,
   // truncation): MPSLCC_FP64, or MPSLCC_BF16X3 inside mixed-precision sweeps
   int gemm_prec = MPSLCC_FP64;
+
+  // tile-shape autotuner of the sigma phases (tc_gemm.cu): best N-tile cap
+  // per (bra, ket, operator, position, phase, sigma precision)
+  struct TuneKey {
+    const void *bra, *ket, *mpo;
+    int l, phase, v;
+    bool operator<(const TuneKey& o) const {
+      if (bra != o.bra) return bra < o.bra;
+      if (ket != o.ket) return ket < o.ket;
+      if (mpo != o.mpo) return mpo < o.mpo;
+      if (l != o.l) return l < o.l;
+      if (phase != o.phase) return phase < o.phase;
+      return v < o.v;
+    }
+  };
+  struct TuneEntry {
+    double bytes = 0;
+    double ms[3] = {0, 0, 0};
+    int tried = 0, best = -1;
+  };
+  std::map<TuneKey, TuneEntry> tune;
 
   cudaStream_t s() const { return stream; }
 };

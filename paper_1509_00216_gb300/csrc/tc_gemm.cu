@@ -59,11 +59,21 @@ struct alignas(64) TcTask {
 namespace {
 
 constexpr int MAX_DEVICES = 128;
-constexpr int STAGES = 4;
 constexpr int A_BYTES = 128 * 128;           // 128 rows x 128 bytes
-constexpr int B_BYTES_MAX = 256 * 128;       // up to 256 rows x 128 bytes
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES_MAX;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int RING_BYTES = 192 * 1024;       // operand stages; a launch's N-tile cap sets their size
+constexpr int MAX_STAGES = 8;
+constexpr int SMEM_BYTES = RING_BYTES + 1024 + 256;
+
+// Stages of the shared-memory ring for a launch whose tasks use N tiles of at
+// most `cap` rows (64, 128 or 256): a stage holds one A tile (128 x 128 B) and
+// one B tile (cap x 128 B), twice in split mode (hi and lo parts).
+__host__ __device__ __forceinline__ int stage_bytes(int cap, bool split) {
+  return (A_BYTES + cap * 128) * (split ? 2 : 1);
+}
+__host__ __device__ __forceinline__ int ring_stages(int cap, bool split) {
+  const int n = RING_BYTES / stage_bytes(cap, split);
+  return n < MAX_STAGES ? n : MAX_STAGES;
+}
 constexpr int ACC_COLS = 256;                // one FP32 accumulator (N <= 256)
 constexpr int TMEM_COLS = 2 * ACC_COLS;      // double-buffered
 constexpr int TC_THREADS = 192;              // TMA warp, MMA warp, 4 epilogue warps
@@ -387,19 +397,21 @@ __device__ __forceinline__ void store_row(const TcTask* T, long long roff, int c
 template <int PREC, bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
                                                                  long long total, int* err,
-                                                                 unsigned long long wait_ns) {
+                                                                 unsigned long long wait_ns, int cap) {
   // Warp roles: warp 0 issues TMA, warp 1 issues MMA (and owns the tensor
   // memory), warps 2..5 drain a double-buffered accumulator, so the loads and
   // products of the next tile overlap the epilogue of the previous one.
   extern __shared__ uint8_t smem_raw[];
-  // split mode keeps hi and lo tiles of both operands: half as many stages
-  constexpr int NST = SPLIT ? STAGES / 2 : STAGES;
-  constexpr int SB = SPLIT ? 2 * STAGE_BYTES : STAGE_BYTES;
+  // every task of the launch has ntile <= cap; the ring holds as many stages
+  // of that size as fit (split mode keeps hi and lo tiles of both operands)
+  const int NST = ring_stages(cap, SPLIT);
+  const int SB = stage_bytes(cap, SPLIT);
+  const int BB = cap * 128;                          // B tile bytes in a stage
   constexpr int KT = PREC == MPSLCC_BF16 ? 64 : 32;  // K elements per 128-byte row
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  uint64_t* empty = full + NST;
-  uint64_t* acc_full = empty + NST;      // [2]
+  uint64_t* full = (uint64_t*)(smem + RING_BYTES);
+  uint64_t* empty = full + MAX_STAGES;
+  uint64_t* acc_full = empty + MAX_STAGES;  // [2]
   uint64_t* acc_empty = acc_full + 2;    // [2]
   uint64_t* drain = acc_empty + 2;       // [1] completion of the MMA thread's issued products
   volatile uint32_t* tslot = (volatile uint32_t*)(drain + 1);
@@ -452,8 +464,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
           tma_load(st, &T->ma, &full[s], kx, row0, tc.b, T->a3d);
           tma_load(st + A_BYTES, &T->mb, &full[s], kx, col0, tc.b, T->b3d);
           if (SPLIT) {
-            tma_load(st + STAGE_BYTES, &T->ma2, &full[s], kx, row0, tc.b, T->a3d);
-            tma_load(st + STAGE_BYTES + A_BYTES, &T->mb2, &full[s], kx, col0, tc.b, T->b3d);
+            tma_load(st + A_BYTES + BB, &T->ma2, &full[s], kx, row0, tc.b, T->a3d);
+            tma_load(st + 2 * A_BYTES + BB, &T->mb2, &full[s], kx, col0, tc.b, T->b3d);
           }
         }
       }
@@ -491,8 +503,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) umma<PREC>(acc, a + 2 * kk, b + 2 * kk, id, (j > 0 || kk > 0) ? 1u : 0u);
           if (SPLIT) {
-            const uint64_t a2 = sdesc(st + STAGE_BYTES);
-            const uint64_t b2 = sdesc(st + STAGE_BYTES + A_BYTES);
+            const uint64_t a2 = sdesc(st + A_BYTES + BB);
+            const uint64_t b2 = sdesc(st + 2 * A_BYTES + BB);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) umma<PREC>(acc, a + 2 * kk, b2 + 2 * kk, id, 1u);
 #pragma unroll
@@ -726,7 +738,7 @@ int tc_ksplit(int prec, int k, int hint) {
 TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long ldb, int m, int n, int k, void* C,
                  int ldc, int rpb, long long bstride, int mode, int ksplit_hint, long long soff = 0,
                  long lo_off = 0, int batch = 1, long long a_bs = 0, long long b_bs = 0, long long c_bs = 0,
-                 long long kstride = 0) {
+                 long long kstride = 0, int cap = 256) {
   TcTask t;
   std::memset(&t, 0, sizeof(t));
   const int KT = prec == MPSLCC_TF32 ? 32 : 64;
@@ -735,7 +747,8 @@ TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long 
   t.a3d = batch > 1 && a_bs != 0;
   t.b3d = batch > 1 && b_bs != 0;
   t.cbatch = batch > 1 ? c_bs : 0;
-  t.ntile = (int)std::min<long>(256, (n + 15) / 16 * 16);
+  MPSLCC_REQUIRE(cap == 64 || cap == 128 || cap == 256, ST_INTERNAL, "N-tile cap");
+  t.ntile = (int)std::min<long>(cap, (n + 15) / 16 * 16);
   auto map = [&](CUtensorMap* mp, const void* base, long rows, long ld, int box, bool three, long long bs) {
     if (three) encode_map3d(c, mp, prec, base, rows, k, ld, batch, bs, box);
     else encode_map(c, mp, prec, base, rows, k, ld, box);
@@ -795,7 +808,7 @@ long long plan_tc(std::vector<TcTask>& t) {
 // set once per (kernel instance, device), the flag kept per device.
 template <int P, bool S>
 void launch_variant(cudaStream_t st, int grid, const TcTask* d_tasks, int ntasks, long long total, int* err,
-                    unsigned long long wait_ns) {
+                    unsigned long long wait_ns, int cap) {
   static std::atomic<bool> attr[MAX_DEVICES];
   int dev = 0;
   cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -805,14 +818,14 @@ void launch_variant(cudaStream_t st, int grid, const TcTask* d_tasks, int ntasks
                "smem attr");
     attr[dev].store(true, std::memory_order_release);
   }
-  tc_gemm_kernel<P, S><<<grid, TC_THREADS, SMEM_BYTES, st>>>(d_tasks, ntasks, total, err, wait_ns);
+  tc_gemm_kernel<P, S><<<grid, TC_THREADS, SMEM_BYTES, st>>>(d_tasks, ntasks, total, err, wait_ns, cap);
 }
 
 void launch_tc_stream(cudaStream_t st, int grid, int prec, const TcTask* d_tasks, int ntasks, long long total,
-                      int* err, unsigned long long wait_ns = WAIT_NS) {
-  if (prec == MPSLCC_BF16X3) launch_variant<MPSLCC_BF16, true>(st, grid, d_tasks, ntasks, total, err, wait_ns);
-  else if (prec == MPSLCC_BF16) launch_variant<MPSLCC_BF16, false>(st, grid, d_tasks, ntasks, total, err, wait_ns);
-  else launch_variant<MPSLCC_TF32, false>(st, grid, d_tasks, ntasks, total, err, wait_ns);
+                      int* err, unsigned long long wait_ns = WAIT_NS, int cap = 256) {
+  if (prec == MPSLCC_BF16X3) launch_variant<MPSLCC_BF16, true>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
+  else if (prec == MPSLCC_BF16) launch_variant<MPSLCC_BF16, false>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
+  else launch_variant<MPSLCC_TF32, false>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
 }
 
 // bound on each mbarrier wait of a context's tensor-core launches
@@ -822,10 +835,10 @@ unsigned long long wait_bound_ns(const Ctx& c) {
   return (unsigned long long)(std::min(s, 60.0) * 1e9);
 }
 
-void launch_tc(Ctx& c, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err) {
+void launch_tc(Ctx& c, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err, int cap = 256) {
   if (total <= 0 || ntasks <= 0) return;
   int grid = (int)std::min<long long>(total, (long long)sm_count(c));
-  launch_tc_stream(c.s(), grid, prec, d_tasks, ntasks, total, err, wait_bound_ns(c));
+  launch_tc_stream(c.s(), grid, prec, d_tasks, ntasks, total, err, wait_bound_ns(c), cap);
   cuda_check(cudaGetLastError(), "tc_gemm launch");
   c.st.kernel_launches++;
   c.st.gemm_launches++;
@@ -878,18 +891,21 @@ struct TcState {
   int layout = -1;      // operand precision class: TF32, BF16 or BF16X3 (the
                         // three-piece six-block layout, serving BF16X3 and BF16X6)
   DBuf lcat, rstk, tt, x, conv, convx, err;
-  // phase-2 K-split partials (FP32) and the segments of their fixed-order sum
-  DBuf ypart[2], segs[2];
-  int nseg[2] = {0, 0};
-  long long seg_tiles[2] = {0, 0};
   std::vector<long> lcat_off, K8, tt_off, x_off;
   std::vector<long> stk_off;
+  std::vector<std::vector<long>> koff8;   // per bra key: channel-block offsets in the padded K
   std::vector<ConvTask> xconv;
-  // task lists per sigma variant: [0] the layout's own precision (TF32, BF16
-  // or BF16X3), [1] BF16X6 (six-block layout only)
-  DBuf t1[2], t2[2];
-  int n1[2] = {0, 0}, n2[2] = {0, 0};
-  long long tiles1[2] = {0, 0}, tiles2[2] = {0, 0};
+  // Task lists per sigma variant v ([0] the layout's own precision: TF32,
+  // BF16 or BF16X3; [1] BF16X6, six-block layout only) and N-tile cap
+  // (TC_CAPS), built on first use; phase 2 keeps its K-split FP32 partials
+  // and the segments of their fixed-order sum.
+  struct Lists {
+    bool built = false;
+    DBuf t1, t2, ypart, segs;
+    int n1 = 0, n2 = 0, nseg = 0;
+    long long tiles1 = 0, tiles2 = 0, seg_tiles = 0;
+  };
+  Lists lists[2][3];
   double bytes1[2] = {0, 0}, bytes2[2] = {0, 0};
 };
 
@@ -1021,104 +1037,175 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     t.soff = pad8(t.cols);
     S->xconv.push_back(t);
   }
-  const long long target = 2LL * sm_count(c);
+  S->koff8 = koff8;
+  // algorithmic bytes of each variant: operands read once and results
+  // written once, per BF16 (or TF32) piece read or written
   for (int v = 0; v < (six ? 2 : 1); ++v) {
-    // v = 0: the layout's own precision; v = 1: BF16X6 (plain BF16 kernel over
-    // all six blocks)
-    const int kp = v == 1 ? MPSLCC_BF16 : layout;
-    const int pcs = v == 1 ? 6 : (six ? 2 : 1);  // pieces read per element
-    std::vector<TcTask> t1, t2;
-    // phase 1: T_w^T = R'_w psi^T for all channels of a class in one tall GEMM
-    const int mode1 = v == 1 ? 5 : (six ? 3 : (layout == MPSLCC_TF32 ? 2 : 1));
+    const int pcs = v == 1 ? 6 : (six ? 2 : 1);
     for (size_t si = 0; si < rf.stk.size(); ++si) {
       const auto& st = rf.stk[si];
-      int bi = st.bidx, ki = st.kidx;
-      const LeftFused::Seg* sg = lf.find_seg(bi, st.cls);
-      size_t g = sg - lf.seg[bi].data();
-      int rb = rf.FRb.d[rf.kb[bi]], rk = rf.FRk.d[rf.kk[ki]], lk = lf.FLk.d[lf.kk[ki]];
-      const long pitch = sp * pad8(rk);
-      const int kk = v == 1 ? (int)pitch : rk;
-      void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + koff8[bi][g]) * es;
-      // split tasks: lo parts in block 2 of both operands (and of the output)
-      const long long so = v == 1 ? S->K8[bi] : 2 * S->K8[bi];
-      t1.push_back(make_task(c, kp, (char*)S->rstk.p + (size_t)S->stk_off[si] * es, pitch,
-                             (char*)S->x.p + (size_t)S->x_off[ki] * es, pitch, st.nw * rb, lk, kk, C,
-                             (int)(sp * S->K8[bi]), rb, pad8(lk), mode1, 1, six ? so : 0, six ? 2 * pad8(rk) : 0));
-      // algorithmic bytes: operands and result once, per piece read or written
-      S->bytes1[v] += (double)es * pcs * ((double)st.nw * rb * rk + (double)lk * rk + (double)st.nw * rb * lk);
+      const double rb = rf.FRb.d[rf.kb[st.bidx]], rk = rf.FRk.d[rf.kk[st.kidx]], lk = lf.FLk.d[lf.kk[st.kidx]];
+      S->bytes1[v] += (double)es * pcs * (st.nw * rb * rk + lk * rk + st.nw * rb * lk);
     }
-    // phase 2: sigma = Lcat Tt^T, split over K so that every tile carries
-    // about the same number of K steps (a balanced persistent schedule).
-    // Split j of a middle sector stores its FP32 partial at its own offset;
-    // one reduction sums the partials in increasing j into the FP64 sigma,
-    // so the result does not depend on the order the splits finish in.
-    long long work = 0;
     for (size_t bi = 0; bi < nbk; ++bi) {
       if (S->K8[bi] == 0) continue;
-      const int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
-      const long kk = v == 1 ? sp * S->K8[bi] : S->K8[bi];
-      const long nt = std::min<long>(256, (rb + 15) / 16 * 16);
-      work += (long long)((lb + 127) / 128) * ((rb + nt - 1) / nt) * ((kk + 63) / 64);
+      const double lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+      S->bytes2[v] += (double)es * pcs * (lb * S->K8[bi] + rb * S->K8[bi]) + 4.0 * lb * rb;
     }
-    const long long kper = std::max(4LL, (work + 4 * target - 1) / (4 * target));
-    std::vector<SplitSeg> segs;
-    std::vector<int> ksv(nbk, 0);
-    long poff = 0;
-    for (size_t bi = 0; bi < nbk; ++bi) {
-      const int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
-      SplitSeg sg;
-      std::memset(&sg, 0, sizeof(sg));
-      sg.out_off = P.off_b[bi];
-      sg.m = lb;
-      sg.n = rb;
-      sg.ldp = (int)((rb + 3) / 4 * 4);   // 16-byte aligned partial rows
-      sg.sstride = (long long)lb * sg.ldp;
-      if (S->K8[bi] > 0) {
-        const long pitch = sp * S->K8[bi];
-        const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
-        const int hint = (int)std::max(1LL, (((long long)kk + 63) / 64 + kper - 1) / kper);
-        ksv[bi] = tc_ksplit(kp, kk, hint);
-        sg.nsplit = ksv[bi];
-        sg.part_off = poff;
-        poff += (long)ksv[bi] * sg.sstride;
-      }
-      segs.push_back(sg);   // nsplit = 0: no channel reaches the sector, sigma is zero there
-    }
-    S->ypart[v].alloc(&c, std::max<long>(poff, 4) * 4);
-    for (size_t bi = 0; bi < nbk; ++bi) {
-      if (S->K8[bi] == 0) continue;
-      int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
-      const long pitch = sp * S->K8[bi];
-      const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
-      const SplitSeg& sg = segs[bi];
-      t2.push_back(make_task(c, kp, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, pitch,
-                             (char*)S->tt.p + (size_t)S->tt_off[bi] * es, pitch, lb, rb, kk,
-                             (float*)S->ypart[v].p + sg.part_off, sg.ldp, 1 << 30, 0, 2, ksv[bi], 0,
-                             (six && v == 0) ? 2 * S->K8[bi] : 0, 1, 0, 0, 0, sg.sstride));
-      S->bytes2[v] += (double)es * pcs * ((double)lb * S->K8[bi] + (double)rb * S->K8[bi]) + 4.0 * lb * rb;
-    }
-    S->nseg[v] = (int)segs.size();
-    S->seg_tiles[v] = plan_split_tiles(segs.data(), (int)segs.size());
-    S->segs[v].alloc(&c, std::max<size_t>(segs.size(), 1) * sizeof(SplitSeg));
-    if (!segs.empty())
-      cuda_check(cudaMemcpyAsync(S->segs[v].p, segs.data(), segs.size() * sizeof(SplitSeg), cudaMemcpyHostToDevice,
-                                 c.s()),
-                 "split segments");
-    S->n1[v] = (int)t1.size();
-    S->n2[v] = (int)t2.size();
-    S->tiles1[v] = plan_tc(t1);
-    S->tiles2[v] = plan_tc(t2);
-    S->t1[v].alloc(&c, std::max<size_t>(t1.size(), 1) * sizeof(TcTask));
-    S->t2[v].alloc(&c, std::max<size_t>(t2.size(), 1) * sizeof(TcTask));
-    if (!t1.empty())
-      cuda_check(cudaMemcpyAsync(S->t1[v].p, t1.data(), t1.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
-                 "tc tasks");
-    if (!t2.empty())
-      cuda_check(cudaMemcpyAsync(S->t2[v].p, t2.data(), t2.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
-                 "tc tasks");
   }
   cuda_check(cudaStreamSynchronize(c.s()), "tc prepare sync");
 }
+
+namespace {
+
+constexpr int TC_CAPS[3] = {256, 128, 64};
+
+// Task lists of sigma variant v with N tiles of at most TC_CAPS[ci] rows.
+void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
+  TcState::Lists& Ls = S->lists[v][ci];
+  if (Ls.built) return;
+  const int cap = TC_CAPS[ci];
+  const int layout = S->layout;
+  const int es = esize(layout);
+  const bool six = layout == MPSLCC_BF16X3;
+  const int sp = six ? 6 : 1;
+  const LeftFused& lf = P.lf;
+  const RightFused& rf = P.rf;
+  const size_t nbk = P.mid_b.size();
+  const long long target = 2LL * sm_count(c);
+  // v = 0: the layout's own precision; v = 1: BF16X6 (plain BF16 kernel over
+  // all six blocks)
+  const int kp = v == 1 ? MPSLCC_BF16 : layout;
+  std::vector<TcTask> t1, t2;
+  // phase 1: T_w^T = R'_w psi^T for all channels of a class in one tall GEMM
+  const int mode1 = v == 1 ? 5 : (six ? 3 : (layout == MPSLCC_TF32 ? 2 : 1));
+  for (size_t si = 0; si < rf.stk.size(); ++si) {
+    const auto& st = rf.stk[si];
+    int bi = st.bidx, ki = st.kidx;
+    const LeftFused::Seg* sg = lf.find_seg(bi, st.cls);
+    size_t g = sg - lf.seg[bi].data();
+    int rb = rf.FRb.d[rf.kb[bi]], rk = rf.FRk.d[rf.kk[ki]], lk = lf.FLk.d[lf.kk[ki]];
+    const long pitch = sp * pad8(rk);
+    const int kk = v == 1 ? (int)pitch : rk;
+    void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + S->koff8[bi][g]) * es;
+    // split tasks: lo parts in block 2 of both operands (and of the output)
+    const long long so = v == 1 ? S->K8[bi] : 2 * S->K8[bi];
+    t1.push_back(make_task(c, kp, (char*)S->rstk.p + (size_t)S->stk_off[si] * es, pitch,
+                           (char*)S->x.p + (size_t)S->x_off[ki] * es, pitch, st.nw * rb, lk, kk, C,
+                           (int)(sp * S->K8[bi]), rb, pad8(lk), mode1, 1, six ? so : 0, six ? 2 * pad8(rk) : 0, 1,
+                           0, 0, 0, 0, cap));
+  }
+  // phase 2: sigma = Lcat Tt^T, split over K so that every tile carries
+  // about the same number of K steps (a balanced persistent schedule).  The
+  // split counts come from an N tiling of 256 whatever the launch's cap, so
+  // every cap stores the same partials.  Split j of a middle sector stores
+  // its FP32 partial at its own offset; one reduction sums the partials in
+  // increasing j into the FP64 sigma, so the result does not depend on the
+  // order the splits finish in.
+  long long work = 0;
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    if (S->K8[bi] == 0) continue;
+    const int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+    const long kk = v == 1 ? sp * S->K8[bi] : S->K8[bi];
+    const long nt = std::min<long>(256, (rb + 15) / 16 * 16);
+    work += (long long)((lb + 127) / 128) * ((rb + nt - 1) / nt) * ((kk + 63) / 64);
+  }
+  const long long kper = std::max(4LL, (work + 4 * target - 1) / (4 * target));
+  std::vector<SplitSeg> segs;
+  std::vector<int> ksv(nbk, 0);
+  long poff = 0;
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    const int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+    SplitSeg sg;
+    std::memset(&sg, 0, sizeof(sg));
+    sg.out_off = P.off_b[bi];
+    sg.m = lb;
+    sg.n = rb;
+    sg.ldp = (int)((rb + 3) / 4 * 4);   // 16-byte aligned partial rows
+    sg.sstride = (long long)lb * sg.ldp;
+    if (S->K8[bi] > 0) {
+      const long pitch = sp * S->K8[bi];
+      const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
+      const int hint = (int)std::max(1LL, (((long long)kk + 63) / 64 + kper - 1) / kper);
+      ksv[bi] = tc_ksplit(kp, kk, hint);
+      sg.nsplit = ksv[bi];
+      sg.part_off = poff;
+      poff += (long)ksv[bi] * sg.sstride;
+    }
+    segs.push_back(sg);   // nsplit = 0: no channel reaches the sector, sigma is zero there
+  }
+  Ls.ypart.alloc(&c, std::max<long>(poff, 4) * 4);
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    if (S->K8[bi] == 0) continue;
+    int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+    const long pitch = sp * S->K8[bi];
+    const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
+    const SplitSeg& sg = segs[bi];
+    t2.push_back(make_task(c, kp, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, pitch,
+                           (char*)S->tt.p + (size_t)S->tt_off[bi] * es, pitch, lb, rb, kk,
+                           (float*)Ls.ypart.p + sg.part_off, sg.ldp, 1 << 30, 0, 2, ksv[bi], 0,
+                           (six && v == 0) ? 2 * S->K8[bi] : 0, 1, 0, 0, 0, sg.sstride, cap));
+  }
+  Ls.nseg = (int)segs.size();
+  Ls.seg_tiles = plan_split_tiles(segs.data(), (int)segs.size());
+  Ls.segs.alloc(&c, std::max<size_t>(segs.size(), 1) * sizeof(SplitSeg));
+  if (!segs.empty())
+    cuda_check(cudaMemcpyAsync(Ls.segs.p, segs.data(), segs.size() * sizeof(SplitSeg), cudaMemcpyHostToDevice, c.s()),
+               "split segments");
+  Ls.n1 = (int)t1.size();
+  Ls.n2 = (int)t2.size();
+  Ls.tiles1 = plan_tc(t1);
+  Ls.tiles2 = plan_tc(t2);
+  Ls.t1.alloc(&c, std::max<size_t>(t1.size(), 1) * sizeof(TcTask));
+  Ls.t2.alloc(&c, std::max<size_t>(t2.size(), 1) * sizeof(TcTask));
+  if (!t1.empty())
+    cuda_check(cudaMemcpyAsync(Ls.t1.p, t1.data(), t1.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
+               "tc tasks");
+  if (!t2.empty())
+    cuda_check(cudaMemcpyAsync(Ls.t2.p, t2.data(), t2.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
+               "tc tasks");
+  Ls.built = true;
+}
+
+// Tile-shape autotuner of the sigma phases.  For every (operator family,
+// position, phase, precision) the first products run once with each N-tile cap
+// (TC_CAPS: 256, 128 and 64 rows, i.e. 4 / 6 / 8 ring stages of BF16 tiles, or
+// 2 / 3 / 4 of split tiles); the cap with the shortest device time is kept
+// for later products of that position, in this and later sweeps, and tuned
+// again when the phase's algorithmic bytes change by more than a fifth.
+// Every cap computes the same numbers (the K splits do not depend on it).
+Ctx::TuneEntry& tune_entry(Ctx& c, const SigmaPlan& P, int phase, int prec, double bytes) {
+  const Ctx::TuneKey key{(const void*)P.fam->bra, (const void*)P.fam->ket, (const void*)P.fam->mpo, P.l, phase, prec};
+  Ctx::TuneEntry& e = c.tune[key];
+  if (!(e.bytes > 0) || std::fabs(bytes - e.bytes) > 0.2 * e.bytes) {
+    e = Ctx::TuneEntry();
+    e.bytes = bytes;
+  }
+  return e;
+}
+
+int tune_choice(const Ctx& c, const Ctx::TuneEntry& e) {
+  if (!c.opts.autotune) return 0;
+  if (e.best >= 0) return e.best;
+  for (int ci = 0; ci < 3; ++ci)
+    if (!(e.tried & (1 << ci))) return ci;
+  return 0;
+}
+
+void tune_record(Ctx& c, Ctx::TuneEntry& e, int ci, double ms) {
+  if (!c.opts.autotune || e.best >= 0) return;
+  if (!(e.tried & (1 << ci)) || ms < e.ms[ci]) e.ms[ci] = ms;
+  e.tried |= 1 << ci;
+  c.st.tune_trials++;
+  if (e.tried == 7) {
+    int b = 0;
+    for (int ci2 = 1; ci2 < 3; ++ci2)
+      if (e.ms[ci2] < e.ms[b]) b = ci2;
+    e.best = b;
+  }
+}
+
+}  // namespace
 
 void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
   tc_prepare(c, P, prec);
@@ -1129,19 +1216,29 @@ void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
     cuda_check(cudaMemcpyAsync(P.xin.p, x, P.nk * sizeof(double), cudaMemcpyDeviceToDevice, c.s()), "sigma in");
   std::vector<ConvTask> xc = S->xconv;
   run_conv(c, S->layout, xc, S->convx);
+  Ctx::TuneEntry& e1 = tune_entry(c, P, 1, prec, S->bytes1[v]);
+  Ctx::TuneEntry& e2 = tune_entry(c, P, 2, prec, S->bytes2[v]);
+  const int c1 = tune_choice(c, e1), c2 = tune_choice(c, e2);
+  build_lists(c, P, S, v, c1);
+  build_lists(c, P, S, v, c2);
+  const TcState::Lists& L1 = S->lists[v][c1];
+  const TcState::Lists& L2 = S->lists[v][c2];
   cudaEventRecord(c.ev_p0, c.s());
-  launch_tc(c, kp, (const TcTask*)S->t1[v].p, S->n1[v], S->tiles1[v], (int*)S->err.p);
+  launch_tc(c, kp, (const TcTask*)L1.t1.p, L1.n1, L1.tiles1, (int*)S->err.p, TC_CAPS[c1]);
   cudaEventRecord(c.ev_p1, c.s());
-  launch_tc(c, kp, (const TcTask*)S->t2[v].p, S->n2[v], S->tiles2[v], (int*)S->err.p);
+  launch_tc(c, kp, (const TcTask*)L2.t2.p, L2.n2, L2.tiles2, (int*)S->err.p, TC_CAPS[c2]);
   cudaEventRecord(c.ev_p2, c.s());
-  launch_splitk_reduce_f32((const SplitSeg*)S->segs[v].p, S->nseg[v], S->seg_tiles[v], (const float*)S->ypart[v].p, y,
-                           c.s());
+  launch_splitk_reduce_f32((const SplitSeg*)L2.segs.p, L2.nseg, L2.seg_tiles, (const float*)L2.ypart.p, y, c.s());
   cuda_check(cudaGetLastError(), "split-K reduction");
   c.st.kernel_launches++;
   check_err(c, S->err);
   float m1 = 0, m2 = 0;
   cudaEventElapsedTime(&m1, c.ev_p0, c.ev_p1);
   cudaEventElapsedTime(&m2, c.ev_p1, c.ev_p2);
+  tune_record(c, e1, c1, m1);
+  tune_record(c, e2, c2, m2);
+  c.st.tc_cap_launches[c1]++;
+  c.st.tc_cap_launches[c2]++;
   c.st.tc_phase1_s += m1 * 1e-3;
   c.st.tc_phase2_s += m2 * 1e-3;
   c.st.tc_phase1_bytes += S->bytes1[v];

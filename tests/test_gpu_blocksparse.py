@@ -137,8 +137,11 @@ def test_tensor_core_sigma_matches_blocksparse_oracle(mpslcc, case, prec, tol):
 def test_tensor_core_environments_match_blocksparse_oracle(mpslcc, case):
     """Environments and fused operators built on the tensor cores (batched
     three-piece-BF16 FP64 emulation, as in mixed-precision sweeps) give a
-    sigma within the emulation's accuracy (about 2^-24 per product, carried
-    through every environment update) of the FP64 oracle."""
+    sigma within the emulation's accuracy of the FP64 oracle.  Each
+    environment update is two products accumulated in FP32 over K up to a few
+    thousand (about sqrt(K) 2^-24 ~ 4e-6 relative each); the middle position
+    of a 24-orbital chain carries about 40 of them from both ends, hence a
+    bound of 1e-4 (measured: 3e-5 at M1 = 1000)."""
     with case.context(tc_environments=True) as ctx:
         for l in case.positions:
             op = mpslcc.OP_H0_11
@@ -146,4 +149,4 @@ def test_tensor_core_environments_match_blocksparse_oracle(mpslcc, case):
             psi = synth.random_vector(n_in, 3000 + l)
             s = ctx.apply_heff(l, op, psi)
             e2, _ = _errs(s, case.oracle(op, l, psi))
-            assert e2 <= 2e-6, (l, e2)
+            assert e2 <= 1e-4, (l, e2)

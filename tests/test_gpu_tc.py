@@ -113,3 +113,28 @@ def test_mixed_precision_lcc_matches_fp64(mpslcc, prec, tol):
     assert abs(e["E0"] - g["E0"]) < 1e-8
     assert abs(e["E2"] - g["E2"]) < tol, (e["E2"], g["E2"])
     assert abs(e["E3"] - g["E3"]) < tol, (e["E3"], g["E3"])
+
+
+@pytest.mark.parametrize("prec", ["BF16X3", "BF16X6", "TF32"])
+def test_autotuner_tries_every_tile_cap_and_results_do_not_depend_on_it(mpslcc, prec):
+    """Repeated products at one position: the tile-shape autotuner runs each
+    sigma phase once with N tiles of at most 256, 128 and 64 rows (4 / 6 / 8
+    or, split, 2 / 3 / 4 pipeline stages), then keeps the fastest.  The K
+    splits do not depend on the tile shape, so every product is the same to
+    the last bit."""
+    k = 6
+    h, V = synth.ab_initio(k, 6, seed=77)
+    with mpslcc.Context(device=0) as ctx:
+        ctx.build_mpo(h, V, 6, 0)
+        ctx.set_spaces(1, 3)
+        ctx.load_mps(1, synth.random_mps(k, 6, 0, M=40, seed=1))
+        l = 2
+        n, _ = ctx.local_dim(l, mpslcc.OP_H0_11)
+        psi = synth.random_vector(n, 77)
+        outs = [ctx.apply_heff(l, mpslcc.OP_H0_11, psi, prec=getattr(mpslcc, prec)) for _ in range(5)]
+        st = ctx.stats()
+    for cap in ("n256", "n128", "n64"):
+        assert st["tc_launches_" + cap] >= 2, (cap, st["tc_launches_" + cap])
+    assert st["tune_trials"] == 6
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])

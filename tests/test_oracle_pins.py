@@ -254,3 +254,18 @@ def test_state_energies_at_the_solution_and_invariances():
         ed = lcc.state_energies(H, H0, phi0, x + d)
         assert ed["J"] > r["E2"]
         assert abs((ed["J"] - r["E2"]) - d @ A @ d) < 1e-12
+
+
+def test_one_site_isometry_reproduces_mps_vector():
+    """P1 psi with psi = the site tensor of l in the one-site layout equals
+    the full expansion of the MPS (Eq. mps1) at every site."""
+    k = 5
+    m = synth.random_mps(k, 5, 1, M=12, seed=8, isometric=False)
+    dets = fci.determinants(k, 3, 2)
+    full = omps.to_vector(m, dets)
+    for l in range(k):
+        entries = omps.local_layout1(m, l)
+        psi = np.array([m["sites"][l][(ia, s, ib)][a, b] if (ia, s, ib) in m["sites"][l] else 0.0
+                        for (ia, a, s, ib, b) in entries])
+        P = omps.isometry1(m, l, dets)
+        np.testing.assert_allclose(P @ psi, full, atol=1e-12)
