@@ -242,6 +242,19 @@ mpslcc_status mpslcc_dmrg_reference(mpslcc_ctx* ctx, int M0, int n_sweeps, doubl
    the wavefunctions of orders above n. */
 mpslcc_status mpslcc_lcc_sweep(mpslcc_ctx* ctx, int M1, int order, int n_sweeps, double* E2_out);
 
+/* One-site sweeps (Implementation section: only the tensor of one site is
+   optimised at a time, a local problem of d M^2 entries instead of the
+   two-site d^2 M^2) of the order-`order` wavefunction at its current bond
+   dimensions: sites 0 .. n_orb-2 left to right, then n_orb-1 .. 1 right to
+   left, each a local linear solve of Eq. 1 (as mpslcc_lcc_sweep) on the
+   one-site local problem, after which the orthogonality centre moves to the
+   neighbouring site without discarding weight.  The bond dimensions do not
+   grow: run two-site sweeps (mpslcc_lcc_sweep) first.  Needs the wavefunction
+   with its centre at site 0 (after a two-site sweep, or loaded after one);
+   E_STATE if it is absent.  Writes the last local Hylleraas value to *J_out;
+   E_NOCONV as mpslcc_lcc_sweep. */
+mpslcc_status mpslcc_lcc_sweep_onesite(mpslcc_ctx* ctx, int order, int n_sweeps, double* J_out);
+
 /* A window of a half sweep of mpslcc_lcc_sweep (Implementation section: the
    sweep optimises one position at a time): `count` two-site steps starting
    at position `first` (0..n_orb-2) and moving towards higher (dir = +1) or
@@ -283,6 +296,16 @@ mpslcc_status mpslcc_local_dim(mpslcc_ctx* ctx, int site, int op, long* n_out, l
    Errors: E_ARG (sizes), E_STATE (MPS for op not present). */
 mpslcc_status mpslcc_apply_heff(mpslcc_ctx* ctx, int site, int op, const double* psi,
                                 double* sigma, long n_in, long n_out, int prec);
+
+/* One-site local problem at site `site` (0..n_orb-1): sigma = P_bra^T O P_ket
+   psi with P the isometry of all sites but `site`; the local vector is the
+   site's tensor in its left-fused layout (bond-(site+1) sectors q ascending,
+   each a row-major block with rows = (s ascending, bond-site sector
+   ascending, index) and columns = the index within q).  Host arrays, as
+   mpslcc_apply_heff. */
+mpslcc_status mpslcc_local_dim1(mpslcc_ctx* ctx, int site, int op, long* n_out, long* n_in);
+mpslcc_status mpslcc_apply_heff1(mpslcc_ctx* ctx, int site, int op, const double* psi, double* sigma, long n_in,
+                                 long n_out, int prec);
 
 /* Same with DEVICE pointers (FP64, on the context stream); no host copies. */
 mpslcc_status mpslcc_apply_heff_device(mpslcc_ctx* ctx, int site, int op, const double* d_psi,

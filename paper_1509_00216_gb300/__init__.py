@@ -29,7 +29,7 @@ FLAG_NOCONV, FLAG_INDEFINITE, FLAG_E2_POSITIVE, FLAG_J_ROSE = 1, 2, 4, 8
 EXPORTED = [
     "mpslcc_default_opts", "mpslcc_create", "mpslcc_destroy", "mpslcc_last_error", "mpslcc_build_mpo",
     "mpslcc_set_spaces", "mpslcc_dmrg_reference", "mpslcc_lcc_sweep", "mpslcc_lcc_sweep_window", "mpslcc_energy",
-    "mpslcc_energy_series",
+    "mpslcc_energy_series", "mpslcc_lcc_sweep_onesite", "mpslcc_local_dim1", "mpslcc_apply_heff1",
     "mpslcc_local_dim",
     "mpslcc_apply_heff", "mpslcc_apply_heff_device", "mpslcc_load_mps", "mpslcc_export_mps",
     "mpslcc_mpo_bond_dims", "mpslcc_export_mpo_site", "mpslcc_get_stats", "mpslcc_reset_stats",
@@ -94,6 +94,9 @@ def _load():
         "mpslcc_lcc_sweep_window": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, dp]),
         "mpslcc_energy": (C.c_int, [vp, C.POINTER(Energies)]),
         "mpslcc_energy_series": (C.c_int, [vp, dp, C.c_int, ip]),
+        "mpslcc_lcc_sweep_onesite": (C.c_int, [vp, C.c_int, C.c_int, dp]),
+        "mpslcc_local_dim1": (C.c_int, [vp, C.c_int, C.c_int, lp, lp]),
+        "mpslcc_apply_heff1": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, C.c_long, C.c_long, C.c_int]),
         "mpslcc_local_dim": (C.c_int, [vp, C.c_int, C.c_int, lp, lp]),
         "mpslcc_apply_heff": (C.c_int, [vp, C.c_int, C.c_int, dp, dp, C.c_long, C.c_long, C.c_int]),
         "mpslcc_apply_heff_device": (C.c_int, [vp, C.c_int, C.c_int, vp, vp, C.c_long, C.c_long, C.c_int]),
@@ -258,6 +261,27 @@ class Context:
         self._check(lib().mpslcc_lcc_sweep_window(self.h, M1, order, first, count, direction, C.byref(e)),
                     soft_noconv=True)
         return e.value
+
+    def lcc_sweep_onesite(self, n_sweeps, order=1):
+        """One-site sweeps at the current bond dimensions (after two-site sweeps)."""
+        e = C.c_double()
+        self._check(lib().mpslcc_lcc_sweep_onesite(self.h, order, n_sweeps, C.byref(e)), soft_noconv=True)
+        return e.value
+
+    def local_dim1(self, site, op):
+        a, b = C.c_long(), C.c_long()
+        self._check(lib().mpslcc_local_dim1(self.h, site, op, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def apply_heff1(self, site, op, psi, prec=FP64):
+        """One-site sigma at `site` (host arrays)."""
+        n_out, n_in = self.local_dim1(site, op)
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        if psi.size != n_in:
+            raise ValueError(f"psi has {psi.size} entries, local dimension is {n_in}")
+        out = np.zeros(n_out)
+        self._check(lib().mpslcc_apply_heff1(self.h, site, op, _dptr(psi), _dptr(out), n_in, n_out, prec))
+        return out
 
     def energy_series(self):
         """E(0), E(1), ..., E(2N+1) of the wavefunctions present (Eq. 2)."""

@@ -284,6 +284,18 @@ mpslcc_status mpslcc_lcc_sweep(mpslcc_ctx* ctx, int M1, int order, int n_sweeps,
   }));
 }
 
+mpslcc_status mpslcc_lcc_sweep_onesite(mpslcc_ctx* ctx, int order, int n_sweeps, double* J_out) {
+  if (ctx) ctx->c.cf.reset();
+  return noconv_status(ctx, guard(ctx, [&](Ctx& c) {
+    need_device(c);
+    MPSLCC_REQUIRE(order >= 1 && order <= Ctx::MAX_ORDER, ST_ARG, "order must be in [1, 8]");
+    MPSLCC_REQUIRE(n_sweeps >= 1, ST_ARG, "n_sweeps must be positive");
+    cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
+    double J = lcc_sweeps1(c, n_sweeps, order);
+    if (J_out) *J_out = J;
+  }));
+}
+
 mpslcc_status mpslcc_lcc_sweep_window(mpslcc_ctx* ctx, int M1, int order, int first, int count, int dir,
                                       double* J_out) {
   if (ctx) ctx->c.cf.reset();
@@ -356,17 +368,18 @@ mpslcc_status mpslcc_local_dim(mpslcc_ctx* ctx, int site, int op, long* n_out, l
 }
 
 static void apply_heff_dev(Ctx& c, int site, int op, const double* d_psi, double* d_sigma, long n_in, long n_out,
-                           int prec) {
+                           int prec, bool one_site = false) {
   need_device(c);
   cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
-  MPSLCC_REQUIRE(site >= 0 && site <= c.k - 2, ST_ARG, "site out of range");
+  MPSLCC_REQUIRE(site >= 0 && site <= c.k - (one_site ? 1 : 2), ST_ARG, "site out of range");
   MPSLCC_REQUIRE(prec >= MPSLCC_FP64 && prec <= MPSLCC_BF16X6, ST_ARG, "bad precision");
   Family& F = family_for(c, op);
   SigmaPlan P;
   const int saved = c.gemm_prec;
   c.gemm_prec = c.opts.tc_environments ? MPSLCC_BF16X3 : MPSLCC_FP64;
   try {
-    make_sigma_plan(c, F, site, P);
+    if (one_site) make_sigma_plan1(c, F, site, P);
+    else make_sigma_plan(c, F, site, P);
   } catch (...) {
     c.gemm_prec = saved;
     throw;
@@ -389,6 +402,41 @@ mpslcc_status mpslcc_apply_heff(mpslcc_ctx* ctx, int site, int op, const double*
     y.alloc(&c, std::max(n_out, 1L) * sizeof(double));
     cuda_check(cudaMemcpyAsync(x.p, psi, n_in * sizeof(double), cudaMemcpyHostToDevice, c.s()), "psi h2d");
     apply_heff_dev(c, site, op, x.d(), y.d(), n_in, n_out, prec);
+    cuda_check(cudaMemcpyAsync(sigma, y.p, n_out * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "sigma d2h");
+    cuda_check(cudaStreamSynchronize(c.s()), "apply sync");
+  });
+}
+
+mpslcc_status mpslcc_local_dim1(mpslcc_ctx* ctx, int site, int op, long* n_out, long* n_in) {
+  return guard(ctx, [&](Ctx& c) {
+    MPSLCC_REQUIRE(site >= 0 && site <= c.k - 1, ST_ARG, "site out of range");
+    MPSLCC_REQUIRE(op >= 0 && op <= 5, ST_ARG, "unknown operator");
+    MPS* bra = (op == MPSLCC_OP_H0_00) ? &c.phi0 : &c.phi1;
+    MPS* ket = (op == MPSLCC_OP_H0_00 || op == MPSLCC_OP_H_10 || op == MPSLCC_OP_S_10) ? &c.phi0 : &c.phi1;
+    MPSLCC_REQUIRE(bra->present && ket->present, ST_STATE, "MPS for this operator not present");
+    std::vector<QN> mid;
+    std::vector<long> off;
+    long nb = 0, nk = 0;
+    one_site_middle(*bra, site, mid, off, nb);
+    one_site_middle(*ket, site, mid, off, nk);
+    if (n_out) *n_out = nb;
+    if (n_in) *n_in = nk;
+  });
+}
+
+mpslcc_status mpslcc_apply_heff1(mpslcc_ctx* ctx, int site, int op, const double* psi, double* sigma, long n_in,
+                                 long n_out, int prec) {
+  return guard(ctx, [&](Ctx& c) {
+    MPSLCC_REQUIRE(psi && sigma, ST_ARG, "null vector");
+    MPSLCC_REQUIRE(n_in >= 0 && n_out >= 0, ST_ARG, "negative vector length");
+    require_finite(psi, (size_t)n_in, "psi");
+    need_device(c);
+    cuda_check(cudaSetDevice(c.device), "cudaSetDevice");
+    DBuf x, y;
+    x.alloc(&c, std::max(n_in, 1L) * sizeof(double));
+    y.alloc(&c, std::max(n_out, 1L) * sizeof(double));
+    cuda_check(cudaMemcpyAsync(x.p, psi, n_in * sizeof(double), cudaMemcpyHostToDevice, c.s()), "psi h2d");
+    apply_heff_dev(c, site, op, x.d(), y.d(), n_in, n_out, prec, true);
     cuda_check(cudaMemcpyAsync(sigma, y.p, n_out * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "sigma d2h");
     cuda_check(cudaStreamSynchronize(c.s()), "apply sync");
   });

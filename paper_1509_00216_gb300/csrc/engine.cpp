@@ -601,7 +601,7 @@ void env_update_right(Ctx& c, Family& F, int p, const RightFused& rf) {
     int rb = rf.FRb.d[j.fb], rk = rf.FRk.d[j.fk];
     int dk = bk.d[j.ik], db = bb.d[j.ib];
     long blkS = (long)rb * rk;
-    const double* Rp = rf.data.d() + j.S->off;
+    const double* Rp = rf.base() + j.S->off;
     const double* Bk = Kt.site[p].rf.d() + Kt.site[p].rf_off[j.ik];
     const double* Bb = B.site[p].rf.d() + B.site[p].rf_off[j.ib];
     ty.push_back(gemm(Rp, Bk, Y + j.yoff, rb, dk, rk, rk, rk, dk, GEMM_TB, j.S->nw, blkS, 0, (long long)rb * dk));
@@ -645,16 +645,18 @@ void build_right_env(Ctx& c, Family& F, int p) {
   env_update_right(c, F, p, rf);
 }
 
-void ensure_envs(Ctx& c, Family& F, int l) {
+void ensure_envs_at(Ctx& c, Family& F, int lb, int rb) {
   int k = F.bra->k;
   if (F.L.empty() || !F.L[0].valid || !F.R[k].valid) boundary_envs(c, F);
-  int b = l;
+  int b = lb;
   while (b > 0 && !F.L[b].valid) --b;
-  for (int p = b; p < l; ++p) build_left_env(c, F, p);
-  int e = l + 2;
+  for (int p = b; p < lb; ++p) build_left_env(c, F, p);
+  int e = rb;
   while (e < k && !F.R[e].valid) ++e;
-  for (int p = e - 1; p >= l + 2; --p) build_right_env(c, F, p);
+  for (int p = e - 1; p >= rb; --p) build_right_env(c, F, p);
 }
+
+void ensure_envs(Ctx& c, Family& F, int l) { ensure_envs_at(c, F, l, l + 2); }
 
 // ---------------------------------------------------------------------------
 // two-site sigma
@@ -674,6 +676,84 @@ void two_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long
   }
 }
 
+// One-site middle sectors of site l: the sectors q of bond l+1 reachable
+// from bond l; the local vector is site l in its left-fused layout, one
+// row-major block [dimFL(q) x d(q)] per sector.
+void one_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long>& off, long& n) {
+  Fused FL = fuse_left(m.bond[l], m.mask[l]);
+  const Sectors& b = m.bond[l + 1];
+  mid.clear();
+  off.clear();
+  n = 0;
+  for (int j = 0; j < b.size(); ++j) {
+    int f = FL.find(b.q[j]);
+    if (f < 0 || FL.d[f] == 0 || b.d[j] == 0) continue;
+    mid.push_back(b.q[j]);
+    off.push_back(n);
+    n += (long)FL.d[f] * b.d[j];
+  }
+}
+
+void form_one_site(Ctx& c, MPS& m, int l, double* psi) {
+  ensure_lf(c, m, l);
+  std::vector<QN> mid;
+  std::vector<long> off;
+  long n;
+  one_site_middle(m, l, mid, off, n);
+  long tot = 0;
+  layout_offsets(m, l, 0, &tot);
+  MPSLCC_REQUIRE(tot == n, ST_INTERNAL, "one-site layout differs from the left-fused site layout");
+  if (n > 0)
+    cuda_check(cudaMemcpyAsync(psi, m.site[l].lf.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c.s()),
+               "one-site vector");
+}
+
+// The right side of a one-site position l: the environment R[l+1] on the
+// bond's sectors, its blocks used in place as the phase-1 stacks.
+static void make_right_env(Ctx& c, Family& F, int l, const std::vector<QN>& kbq, const std::vector<QN>& kkq,
+                           RightFused& rf) {
+  MPS& B = *F.bra;
+  MPS& Kt = *F.ket;
+  const Env& E = F.R[l + 1];
+  MPSLCC_REQUIRE(E.valid, ST_INTERNAL, "right environment missing");
+  auto bond_space = [](const Sectors& s) {
+    Fused f;
+    for (int i = 0; i < s.size(); ++i) {
+      f.q.push_back(s.q[i]);
+      f.d.push_back(s.d[i]);
+      f.pc.push_back({Piece{i, -1, s.d[i], 0}});
+    }
+    return f;
+  };
+  rf.p = l;
+  rf.FRb = bond_space(B.bond[l + 1]);
+  rf.FRk = bond_space(Kt.bond[l + 1]);
+  set_keys(rf.FRb, kbq, rf.kb, rf.kb_of);
+  set_keys(rf.FRk, kkq, rf.kk, rf.kk_of);
+  std::map<std::pair<int, int>, const EnvPair*> pairs;
+  for (const auto& e : E.pairs) pairs[{e.ib, e.ik}] = &e;
+  const MpoBond& mb = F.mpo->bond[l + 1];
+  rf.stk.clear();
+  rf.sidx.clear();
+  for (size_t ki = 0; ki < rf.kk.size(); ++ki) {
+    const int ik = rf.kk[ki];
+    for (size_t cl = 0; cl < mb.class_dq.size(); ++cl) {
+      const int ib = rf.FRb.find(rf.FRk.q[ik] + mb.class_dq[cl]);
+      if (ib < 0 || rf.kb_of[ib] < 0) continue;
+      auto it = pairs.find({ib, ik});
+      if (it == pairs.end()) continue;
+      MPSLCC_REQUIRE(it->second->cls == (int)cl && it->second->nw == mb.class_n[cl], ST_INTERNAL,
+                     "environment pair class mismatch");
+      RightFused::Stk st{(int)ki, (int)cl, rf.kb_of[ib], it->second->nw, it->second->off};
+      rf.sidx[{(int)ki, (int)cl}] = (int)rf.stk.size();
+      rf.stk.push_back(st);
+    }
+  }
+  rf.data.release();
+  rf.ext = E.data.d();
+  rf.size = E.size;
+}
+
 void build_fused_ahead(Ctx& c, Family& F, int l, bool right_side, FusedAhead& A) {
   std::vector<long> ob, ok;
   long nb = 0, nk = 0;
@@ -685,6 +765,8 @@ void build_fused_ahead(Ctx& c, Family& F, int l, bool right_side, FusedAhead& A)
   A.l = l;
   A.right = right_side;
 }
+
+static void finish_sigma_plan(Ctx& c, SigmaPlan& P);
 
 void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead) {
   ensure_envs(c, F, l);
@@ -709,6 +791,27 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead) 
     make_right_fused(c, F, l + 1, P.mid_b, P.mid_k, P.rf);
   }
   if (ahead) ahead->l = -1;
+  finish_sigma_plan(c, P);
+}
+
+void make_sigma_plan1(Ctx& c, Family& F, int l, SigmaPlan& P) {
+  ensure_envs_at(c, F, l, l + 1);
+  P.l = l;
+  P.fam = &F;
+  P.one_site = true;
+  one_site_middle(*F.bra, l, P.mid_b, P.off_b, P.nb);
+  one_site_middle(*F.ket, l, P.mid_k, P.off_k, P.nk);
+  {
+    StageTimer tm(c, &c.st.t_fuse_left);
+    make_left_fused(c, F, l, P.mid_b, P.mid_k, P.lf);
+  }
+  make_right_env(c, F, l, P.mid_b, P.mid_k, P.rf);
+  finish_sigma_plan(c, P);
+}
+
+// Intermediate buffers and the task lists of both sigma phases of a plan
+// whose fused left operator and right operator are in place.
+static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
   const LeftFused& lf = P.lf;
   const RightFused& rf = P.rf;
   P.tt_off.assign(P.mid_b.size(), 0);
@@ -729,7 +832,7 @@ void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead) 
     MPSLCC_REQUIRE(sg && sg->kidx == ki, ST_INTERNAL, "sigma plan: segment/stack mismatch");
     int dFRk = rf.FRk.d[rf.kk[ki]], dFRb = rf.FRb.d[rf.kb[bi]];
     int dFLk = lf.FLk.d[lf.kk[ki]];
-    t1.push_back(gemm(rf.data.d() + S.off, P.xin.d() + P.off_k[ki], P.tt.d() + P.tt_off[bi] + sg->koff, dFRb, dFLk,
+    t1.push_back(gemm(rf.base() + S.off, P.xin.d() + P.off_k[ki], P.tt.d() + P.tt_off[bi] + sg->koff, dFRb, dFLk,
                       dFRk, dFRk, dFRk, (int)lf.K[bi], GEMM_TB, S.nw, (long long)dFRb * dFRk, 0, sg->width));
     fl += 2.0 * S.nw * (double)dFRb * dFLk * dFRk;
   }
@@ -863,7 +966,7 @@ void sigma_diag(Ctx& c, SigmaPlan& P, double* diag) {
     double* DR = DL + (long)nw * dl;
     off += (long)nw * (dl + dr);
     gt.push_back({lf.data.d() + lf.off[bi] + sg->koff, DL, nw, dl, (long long)sg->width, (long long)K + 1});
-    gt.push_back({rf.data.d() + S.off, DR, nw, dr, (long long)dl * 0 + (long long)dr * rf.FRk.d[rf.kk[bi]],
+    gt.push_back({rf.base() + S.off, DR, nw, dr, (long long)dr * rf.FRk.d[rf.kk[bi]],
                   (long long)rf.FRk.d[rf.kk[bi]] + 1});
     maxe = std::max(maxe, nw * std::max(dl, dr));
     mt.push_back(gemm(DL, DR, diag + P.off_b[bi], dl, dr, nw, dl, dr, dr, GEMM_TA));

@@ -130,7 +130,10 @@ struct LeftFused {
   }
 };
 
-// R'[w] of site p (w on MPO bond p), on the fused spaces FR_p.
+// R'[w] of site p (w on MPO bond p), on the fused spaces FR_p.  For a
+// one-site position the right side is the environment R[p+1] itself (spaces
+// = the bond's sectors, one piece each): `ext` then points at the
+// environment's data, which the plan does not own.
 struct RightFused {
   int p = -1;
   Fused FRb, FRk;
@@ -139,7 +142,9 @@ struct RightFused {
   std::vector<Stk> stk;
   std::map<std::pair<int, int>, int> sidx;  // (ket key, class) -> stack
   DBuf data;
+  const double* ext = nullptr;
   long size = 0;
+  const double* base() const { return ext ? ext : data.d(); }
 };
 
 // Fused operator of one side of two-site position l, built ahead of time
@@ -157,9 +162,11 @@ struct FusedAhead {
   RightFused rf;
 };
 
-// Two-site sigma plan at position l.
+// Sigma plan at two-site position l (sites l, l+1) or, with one_site, at
+// site l alone.
 struct SigmaPlan {
   int l = -1;
+  bool one_site = false;
   Family* fam = nullptr;
   LeftFused lf;
   RightFused rf;
@@ -360,7 +367,11 @@ void env_update_left(Ctx& c, Family& F, int p, const LeftFused& lf);
 void env_update_right(Ctx& c, Family& F, int p, const RightFused& rf);
 
 void two_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long>& off, long& n);
+void one_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long>& off, long& n);
 void make_sigma_plan(Ctx& c, Family& F, int l, SigmaPlan& P, FusedAhead* ahead = nullptr);
+void make_sigma_plan1(Ctx& c, Family& F, int l, SigmaPlan& P);   // one-site plan at site l
+void form_one_site(Ctx& c, MPS& m, int l, double* psi);            // site l in the one-site layout
+void ensure_envs_at(Ctx& c, Family& F, int lb, int rb);             // L up to bond lb, R down to bond rb
 void build_fused_ahead(Ctx& c, Family& F, int l, bool right_side, FusedAhead& A);
 void sigma_apply(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec);
 void sigma_diag(Ctx& c, SigmaPlan& P, double* diag);
@@ -381,6 +392,7 @@ void init_random_mps(Ctx& c, MPS& m, int M, bool frozen, unsigned long long seed
 double dmrg_reference(Ctx& c, int M0, int n_sweeps);
 double lcc_sweeps(Ctx& c, int M1, int n_sweeps, int order = 1);
 double lcc_window(Ctx& c, int M1, int first, int count, int dir, int order = 1);
+double lcc_sweeps1(Ctx& c, int n_sweeps, int order = 1);
 void compute_series(Ctx& c);
 void compute_e3(Ctx& c);
 void compute_energies(Ctx& c);

@@ -858,6 +858,11 @@ double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket,
                  const std::vector<RhsTerm>& extra, int l, int prec, int rprec, DBuf& xb, int* its_out,
                  bool* indef_out) {
   long n = P11.nk, n0 = P10.nk, ns = PS.nk;
+  // local vectors of the plans' position: two-site, or site l alone
+  auto form = [&](MPS& m, double* v) {
+    if (P11.one_site) form_one_site(c, m, l, v);
+    else form_two_site(c, m, l, v);
+  };
   xb.alloc(&c, std::max(n, 1L) * sizeof(double));
   DBuf bb, ub, sb, dg, p0, pt;
   std::unique_ptr<StageTimer> trhs(new StageTimer(c, &c.st.t_rhs));
@@ -866,12 +871,12 @@ double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket,
   sb.alloc(&c, std::max(n, 1L) * sizeof(double));
   dg.alloc(&c, std::max(n, 1L) * sizeof(double));
   p0.alloc(&c, std::max(ns, 1L) * sizeof(double));
-  form_two_site(c, c.phi0, l, p0.d());
+  form(c.phi0, p0.d());
   sigma_apply(c, PS, p0.d(), ub.d(), rprec);    // v = P^T Phi0
   const double* tin = p0.d();
   if (&tket != &c.phi0) {
     pt.alloc(&c, std::max(n0, 1L) * sizeof(double));
-    form_two_site(c, tket, l, pt.d());
+    form(tket, pt.d());
     tin = pt.d();
   }
   sigma_apply(c, P10, tin, sb.d(), rprec);      // P^T O Phi(n-1)
@@ -882,7 +887,7 @@ double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket,
     DBuf pk, yk;
     pk.alloc(&c, std::max(t.P->nk, 1L) * sizeof(double));
     yk.alloc(&c, std::max(n, 1L) * sizeof(double));
-    form_two_site(c, *t.ket, l, pk.d());
+    form(*t.ket, pk.d());
     sigma_apply(c, *t.P, pk.d(), yk.d(), rprec);
     launch_axpy(n, t.coef, yk.d(), bb.d(), c.s());
     launch_axpy(n, -t.coef * t.sref, ub.d(), bb.d(), c.s());
@@ -894,7 +899,7 @@ double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket,
     u = ub.d();
   }
   project(c, u, bb.d(), n);
-  form_two_site(c, target, l, xb.d());
+  form(target, xb.d());
   sigma_diag(c, P11, dg.d());
   trhs.reset();
   std::unique_ptr<StageTimer> tsol(new StageTimer(c, &c.st.t_solve));
@@ -1107,6 +1112,70 @@ struct LccRun {
     return J;
   }
 
+  // One one-site step at site l (Implementation section: one tensor is
+  // optimised at a time): the local linear solve gives the new tensor of
+  // site l; the orthogonality centre then moves to site l+1 (right) or l-1
+  // (left) through the density-matrix split of the two-site product of the
+  // new tensor and its neighbour, keeping the bond's current total dimension
+  // (the product's rank does not exceed it: nothing is discarded).  The
+  // environments of the moved bond are rebuilt from the new tensors.
+  double step1(int l, bool right, int sw) {
+    std::vector<Family*> fams = families();
+    std::vector<std::unique_ptr<SigmaPlan>> plans;
+    {
+      StageTimer tm(c, &c.st.t_plan);
+      for (size_t i = 0; i < fams.size(); ++i) {
+        plans.emplace_back(new SigmaPlan());
+        make_sigma_plan1(c, *fams[i], l, *plans.back());
+      }
+      if (prec != MPSLCC_FP64) tc_prepare(c, *plans[0], MPSLCC_BF16X3);
+    }
+    std::vector<RhsTerm> extra;
+    for (size_t i = 0; i < fx.size(); ++i) extra.push_back({plans[3 + i].get(), xket[i], xcoef[i], xsref[i]});
+    DBuf xb;
+    int its = 0;
+    bool indef = false;
+    const double J = lcc_local(c, *target, *plans[0], *plans[1], *tket, tscalar, *plans[2], extra, l, prec, rprec, xb,
+                               &its, &indef);
+    if (J > J_prev + 1e-6 * std::max(1e-12, std::fabs(J_prev))) c.cf.j_rise++;
+    J_prev = J;
+    plans.clear();
+    const int k = c.k;
+    MPS& m = *target;
+    const int nb = right ? l + 1 : l;   // bond the centre moves across
+    const bool moves = right ? l + 1 <= k - 1 : l >= 1;
+    {
+      StageTimer tm(c, &c.st.t_trunc);
+      set_site_lf(c, m, l, std::move(xb));
+      if (moves) {
+        const int p = right ? l : l - 1;  // two-site position of the split
+        std::vector<QN> mid;
+        std::vector<long> off;
+        long n2 = 0;
+        two_site_middle(m, p, mid, off, n2);
+        DBuf psi;
+        psi.alloc(&c, std::max(n2, 1L) * sizeof(double));
+        form_two_site(c, m, p, psi.d());
+        const int keep = m.bond[nb].total();
+        truncate(c, m, p, psi.d(), keep, right);
+      }
+    }
+    for (Family* F : fams) {
+      invalidate_site(*F, l);
+      if (moves) invalidate_site(*F, right ? l + 1 : l - 1);
+    }
+    StageTimer tenv(c, &c.st.t_env);
+    if (moves)
+      for (Family* F : fams) {
+        if (right) build_left_env(c, *F, l);
+        else build_right_env(c, *F, l);
+      }
+    if (c.opts.verbose)
+      fprintf(stderr, "[lcc%d one-site] sweep %d %s l=%d its=%d%s J=%.12f\n", order, sw, right ? "R" : "L", l, its,
+              indef ? " (minres)" : "", J);
+    return J;
+  }
+
   void finish(double J) {
     if (order == 1) {
       c.J = J;
@@ -1157,6 +1226,28 @@ double lcc_sweeps(Ctx& c, int M1, int n_sweeps, int order) {
   }
   cudaEventDestroy(t0);
   cudaEventDestroy(t1);
+  run.finish(J);
+  return J;
+}
+
+// One-site sweeps of the order-n wavefunction at its current bond
+// dimensions: sites 0 .. k-2 left to right, then k-1 .. 1 right to left.
+// Needs the orthogonality centre at site 0 (after a full two-site sweep, or
+// a state exported after one).
+double lcc_sweeps1(Ctx& c, int n_sweeps, int order) {
+  const int k = c.k;
+  MPSLCC_REQUIRE(c.phi_of(order)->present, ST_STATE,
+                 "one-site sweeps keep the bond dimensions of an existing wavefunction: sweep it with "
+                 "two-site sweeps (or load it) first");
+  const int M = 1 << 30;
+  LccRun run(c, M, order);
+  GemmPrec gp(c, run.prec != MPSLCC_FP64 ? MPSLCC_BF16X3 : MPSLCC_FP64);
+  double J = 0;
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    for (int l = 0; l <= k - 2; ++l) J = run.step1(l, true, sw);
+    for (int l = k - 1; l >= 1; --l) J = run.step1(l, false, sw);
+    if (order == 1) c.sweeps_done++;
+  }
   run.finish(J);
   return J;
 }

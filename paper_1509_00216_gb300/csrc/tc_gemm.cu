@@ -1009,7 +1009,7 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     int rb = rf.FRb.d[rf.kb[st.bidx]], rk = rf.FRk.d[rf.kk[st.kidx]];
     ConvTask t;
     std::memset(&t, 0, sizeof(t));
-    t.src = rf.data.d() + st.off;
+    t.src = rf.base() + st.off;
     t.dst = (char*)S->rstk.p + (size_t)S->stk_off[si] * es;
     t.rows = st.nw * rb;
     t.cols = rk;
