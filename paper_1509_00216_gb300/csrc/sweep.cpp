@@ -855,7 +855,7 @@ struct RhsTerm {
 // (the right-hand side in `rprec`); xb receives x.  Returns the local
 // Hylleraas value J = x.Ax - 2 x.b.
 double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket, double tscalar, SigmaPlan& PS,
-                 const std::vector<RhsTerm>& extra, int l, int prec, int rprec, DBuf& xb, int* its_out,
+                 const std::vector<RhsTerm>& extra, int l, int prec, int rprec, double n00, DBuf& xb, int* its_out,
                  bool* indef_out) {
   long n = P11.nk, n0 = P10.nk, ns = PS.nk;
   // local vectors of the plans' position: two-site, or site l alone
@@ -892,9 +892,19 @@ double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket,
     launch_axpy(n, t.coef, yk.d(), bb.d(), c.s());
     launch_axpy(n, -t.coef * t.sref, ub.d(), bb.d(), c.s());
   }
+  // The local form of J(Q P x) is x^T P^T Q A Q P x - 2 x^T P^T Q b with
+  // P^T Q A Q P = P^T A P - v w^T - w v^T + (Phi0^T A Phi0) v v^T,
+  // w = P^T A Phi0, A = H0 - E0: for the reference (an H0 eigenvector up to
+  // its solver residual) w and Phi0^T A Phi0 vanish, so the local matrix is
+  // P^T A P itself, and b_loc above is P^T Q b.  Only when Phi0 lies in the
+  // range of P (|v|^2 = <Phi0|Phi0>, always at exact bond dimension) is v a
+  // null direction of P^T A P; it is then projected out so that Phi1 stays
+  // orthogonal to Phi0.  Projecting v out when |v| < 1 would remove a
+  // legitimate direction of the local space (P v is not Phi0) and make the
+  // sweeps non-variational.
   double vn = std::sqrt(std::max(0.0, dev_dot(c, ub.d(), ub.d(), n)));
   const double* u = nullptr;
-  if (vn > 1e-10) {
+  if (vn > 1e-10 && vn * vn >= (1.0 - 1e-9) * n00) {
     launch_scale(n, 1.0 / vn, ub.d(), c.s());
     u = ub.d();
   }
@@ -974,6 +984,8 @@ double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket,
   return J;
 }
 
+double expect_fp64(Ctx& c, MPS* bra, int mpo, MPS* ket);
+
 namespace {
 
 double expect_norm(Ctx& c, MPS* bra, int mpo, MPS* ket);
@@ -992,6 +1004,7 @@ struct LccRun {
   std::vector<MPS*> xket;
   std::vector<double> xcoef, xsref;
   double J_prev = HUGE_VAL;
+  double n00 = 1.0;           // <Phi0|Phi0>
   std::vector<FusedAhead> ahead;
 
   LccRun(Ctx& c_, int M1_, int order_) : c(c_), M1(M1_), order(order_) {
@@ -1041,6 +1054,7 @@ struct LccRun {
         xsref.push_back(expect_norm(c, &c.phi0, MPO_ID, c.phi_of(j)));
       }
     }
+    n00 = expect_fp64(c, &c.phi0, MPO_ID, &c.phi0);
     // the wavefunctions of higher orders depend on this one
     c.clear_orders_above(order);
     c.series_valid = false;
@@ -1078,8 +1092,8 @@ struct LccRun {
     DBuf xb;
     int its = 0;
     bool indef = false;
-    const double J = lcc_local(c, *target, *plans[0], *plans[1], *tket, tscalar, *plans[2], extra, l, prec, rprec, xb,
-                               &its, &indef);
+    const double J = lcc_local(c, *target, *plans[0], *plans[1], *tket, tscalar, *plans[2], extra, l, prec, rprec, n00,
+                               xb, &its, &indef);
     // within a sweep the local minima do not rise, up to truncation effects
     if (J > J_prev + 1e-6 * std::max(1e-12, std::fabs(J_prev))) c.cf.j_rise++;
     J_prev = J;
@@ -1135,8 +1149,8 @@ struct LccRun {
     DBuf xb;
     int its = 0;
     bool indef = false;
-    const double J = lcc_local(c, *target, *plans[0], *plans[1], *tket, tscalar, *plans[2], extra, l, prec, rprec, xb,
-                               &its, &indef);
+    const double J = lcc_local(c, *target, *plans[0], *plans[1], *tket, tscalar, *plans[2], extra, l, prec, rprec, n00,
+                               xb, &its, &indef);
     if (J > J_prev + 1e-6 * std::max(1e-12, std::fabs(J_prev))) c.cf.j_rise++;
     J_prev = J;
     plans.clear();

@@ -146,6 +146,17 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// Brings a task's tensor maps into the TMA unit's descriptor cache ahead of
+// its first load.
+__device__ __forceinline__ void prefetch_maps(const TcTask* T, bool split) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&T->ma) : "memory");
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&T->mb) : "memory");
+  if (split) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&T->ma2) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&T->mb2) : "memory");
+  }
+}
+
 __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z,
                                          int three) {
   if (three) tma_load_3d(dst, map, bar, x, y, z);
@@ -446,10 +457,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
       uint32_t it = 0;
-      int ti = 0;
+      int ti = 0, prefetched = -1;
       for (long long tile = blockIdx.x; tile < total && !*s_abort; tile += gridDim.x) {
         ti = next_tc(tasks, ntasks, tile, ti);
         const TcTask* T = &tasks[ti];
+        if (prefetched < ti) {
+          // descriptors of this task and of the next one
+          if (prefetched < ti - 1 || prefetched < 0) prefetch_maps(T, SPLIT);
+          if (ti + 1 < ntasks) prefetch_maps(&tasks[ti + 1], SPLIT);
+          prefetched = ti + 1;
+        }
         const TileCoord tc = tile_coord(T, tile);
         const int kt0 = tc.ks * T->kchunk;
         const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;

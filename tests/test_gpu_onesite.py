@@ -78,9 +78,11 @@ def test_one_site_sweeps_reach_the_exact_energies(mpslcc):
 
 @pytest.mark.parametrize("prec", ["FP64", "BF16X3"])
 def test_one_site_sweeps_at_truncated_bond_dimension(mpslcc, prec):
-    """From two-site sweeps at M1 = 64, one-site sweeps keep the bond
-    dimensions and do not raise the Hylleraas value; the energies of the
-    resulting states equal the oracle's evaluation of the exported states."""
+    """From two-site sweeps at M1 = 64, one-site sweeps do not raise the
+    Hylleraas value, and the energies of the resulting states equal the
+    oracle's evaluation of the exported states.  Bond dimensions never grow;
+    they drop to the rank where the two-site truncation had kept zero-weight
+    states to fill M (bond 1 holds at most 4 states of weight)."""
     c = synth.config(0)
     dets = fci.determinants(8, 4, 4)
     H = fci.build_hamiltonian(c["h"], c["V"], dets)
@@ -97,7 +99,8 @@ def test_one_site_sweeps_at_truncated_bond_dimension(mpslcc, prec):
         e = ctx.energy()
         p0, p1 = ctx.export_mps(0), ctx.export_mps(1)
     dims1 = [sum(s[2] for s in b) for b in p1["bonds"]]
-    assert dims1 == dims2
+    assert all(d1 <= d2 for d1, d2 in zip(dims1, dims2)), (dims1, dims2)
+    assert dims1[4] == dims2[4] == 64
     assert e["E2"] <= J2 + 1e-9, (e["E2"], J2)
     o = lcc.state_energies(H, H0, omps.to_vector(p0, dets), omps.to_vector(p1, dets))
     assert abs(e["E2"] - o["E2"]) <= 1e-10 and abs(e["E3"] - o["E3"]) <= 1e-10
