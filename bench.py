@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the mixed-vs-FP64 comparison on a window of middle positions")
     ap.add_argument("--compare-window", type=int, default=4)
+    ap.add_argument("--verbose", type=int, default=0,
+                    help="library verbosity (2: per-truncation stage times on stderr)")
+    ap.add_argument("--partition", default=None,
+                    help="CORE,ACTIVE: override the workload's orbital partition (core and active orbital counts)")
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="profiling mode: N sigma products at the middle position inside NVTX range 'sigma'")
     return ap.parse_args()
@@ -162,8 +166,7 @@ def _o2_workload(cfg, M1):
     L, R = env(l), env(l + 2)
     _, _, n = bs.local_blocks(m, l)
     psi = synth.random_vector(n, 3)
-    classes = dict(zip(mpo.bond_classes[l + 1], mpo.class_n[l + 1]))
-    return dict(mpo=mpo, mps=m, l=l, L=L, R=R, psi=psi, n=n, flops=sigma_flops(m, l, classes), name=c["name"])
+    return dict(mpo=mpo, mps=m, l=l, L=L, R=R, psi=psi, n=n, flops=sigma_flops(mpo, m, l), name=c["name"])
 
 
 def o2_sigma_seconds(w, budget_s):
@@ -184,45 +187,61 @@ def o2_description(w, M1):
     return (f"CPU oracle (oracle.blocksparse, FP64 numpy/OpenBLAS) sigma of H0 at the middle position l={w['l']} "
             f"of {w['name']}: random block-sparse MPS with the workload's orbitals, electrons and M1={M1} sector "
             f"budget (n_local={w['n']}), random environment blocks of the oracle's own MPO classes; flops = the "
-            f"two-phase sigma accounting of the same sector tables ({w['flops']:.3e} per sigma)")
+            f"two-phase sigma accounting of the same sector tables, non-zero local pieces of the fused operators "
+            f"only ({w['flops']:.3e} per sigma)")
 
 
-def sigma_flops(mps, l, mpo_class_sizes):
-    """Algorithmic flops of one sigma (bra = ket = mps, position l): phase 1
-    T_w^T = R'_w psi^T summed over the channel classes of the middle MPO
-    bond, phase 2 sigma = [L'_w ...][T_w; ...] with K = sum over classes of
-    channels x ket fused-left dimension.  mpo_class_sizes maps the class
-    quantum-number change (dN, d2Sz) to its channel count."""
+def sigma_flops(mpo, mps, l):
+    """Algorithmic flops of one sigma (bra = ket = mps, position l) on the
+    oracle's own MPO: phase 1 T_w^T = R'_w psi^T and phase 2
+    sigma = [L'_w ...][T_w; ...], counted block product by block product over
+    the local pieces (s_out, s_in) that channel w's fused operator can hold
+    (those its site tensor reaches; the rest of a fused block is zero)."""
+    import numpy as np
     LQ = [(0, 0), (1, 1), (1, -1), (2, 0)]
+    mid = l + 1
 
-    def fl(bond, mask):
+    def masks(y, left):
+        # channel (class, position) on bond l+1 -> set of (s_out, s_in)
+        m = {}
+        for (c0, c1, so, si), Wm in mpo.W[y].items():
+            nz = Wm.tocoo()
+            for r, q in zip(nz.row, nz.col):
+                key = (c1, int(q)) if left else (c0, int(r))
+                m.setdefault(key, set()).add((so, si))
+        return m
+
+    mL, mR = masks(l, True), masks(l + 1, False)
+
+    def pieces_left(bond, mask):
         d = {}
         for s in mask:
             for (n, sz, dim) in bond:
-                q = (n + LQ[s][0], sz + LQ[s][1])
-                d[q] = d.get(q, 0) + dim
+                d.setdefault((n + LQ[s][0], sz + LQ[s][1]), {})[s] = dim
         return d
 
-    def fr(mask, bond):
+    def pieces_right(mask, bond):
         d = {}
         for s in mask:
             for (n, sz, dim) in bond:
-                q = (n - LQ[s][0], sz - LQ[s][1])
-                d[q] = d.get(q, 0) + dim
+                d.setdefault((n - LQ[s][0], sz - LQ[s][1]), {})[s] = dim
         return d
 
-    FL = fl(mps["bonds"][l], mps["masks"][l])
-    FR = fr(mps["masks"][l + 1], mps["bonds"][l + 2])
-    mid = [q for q in FL if q in FR]
+    FL = pieces_left(mps["bonds"][l], mps["masks"][l])
+    FR = pieces_right(mps["masks"][l + 1], mps["bonds"][l + 2])
+    tot = lambda p: sum(p.values())
+    midq = [q for q in FL if q in FR]
     f = 0.0
-    for qb in mid:
-        K = 0
-        for dq, nw in mpo_class_sizes.items():
+    for qb in midq:
+        for cl, dq in enumerate(mpo.bond_classes[mid]):
             qk = (qb[0] - dq[0], qb[1] - dq[1])
-            if qk in FL and qk in FR:
-                K += nw * FL[qk]
-                f += 2.0 * nw * FR[qb] * FL[qk] * FR[qk]
-        f += 2.0 * FL[qb] * FR[qb] * K
+            if qk not in FL or qk not in FR:
+                continue
+            for w in range(mpo.class_n[mid][cl]):
+                for so, si in mR.get((cl, w), ()):
+                    f += 2.0 * FR[qb].get(so, 0) * FR[qk].get(si, 0) * tot(FL[qk])
+                for so, si in mL.get((cl, w), ()):
+                    f += 2.0 * FL[qb].get(so, 0) * FL[qk].get(si, 0) * tot(FR[qb])
     return f
 
 
@@ -330,10 +349,12 @@ def gpu_arm(args, rank, world, local_rank):
         td.init_process_group("nccl")
     torch.cuda.set_device(local_rank)
     c = synth.config(args.config)
+    if args.partition:
+        c["n_core"], c["n_active"] = (int(x) for x in args.partition.split(","))
     M0 = args.M0 or c["M0"]
     M1 = args.M1 or c["M1"]
     prec = PREC[args.prec]
-    ctx = mp.Context(device=local_rank, prec=prec, tol=1e-8, max_iter=60, torch_memory=True,
+    ctx = mp.Context(device=local_rank, prec=prec, tol=1e-8, max_iter=60, torch_memory=True, verbose=args.verbose,
                      init_guess=1 if args.dmrg_init == "product" else 0)
     ctx.build_mpo(c["h"], c["V"], c["n_alpha"] + c["n_beta"], 0)
     ctx.set_spaces(c["n_core"], c["n_active"])

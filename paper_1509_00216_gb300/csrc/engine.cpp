@@ -184,16 +184,48 @@ void run_copies(Ctx& c, std::vector<CopyTask>& t) {
   c.st.kernel_launches++;
 }
 
-double dev_dot(Ctx& c, const double* x, const double* y, long n) {
-  if (n <= 0) return 0.0;
+static unsigned int* dot_ticket(Ctx& c) {
+  if (!c.red_ticket.p) {
+    c.red_ticket.alloc(&c, 256);
+    cuda_check(cudaMemsetAsync(c.red_ticket.p, 0, 256, c.s()), "dot ticket");
+  }
   c.red.ensure(&c, 4096 * sizeof(double));
   c.red_out.ensure(&c, 256 * sizeof(double));
-  launch_dot(x, y, n, c.red_out.d(), c.red.d(), c.s());
-  c.st.kernel_launches += 2;
+  return (unsigned int*)c.red_ticket.p;
+}
+
+double dev_dot(Ctx& c, const double* x, const double* y, long n) {
+  if (n <= 0) return 0.0;
+  unsigned int* tk = dot_ticket(c);
+  launch_dot_fused(x, y, nullptr, nullptr, n, c.red_out.d(), c.red.d(), tk, c.s());
+  c.st.kernel_launches++;
   double r = 0;
   cuda_check(cudaMemcpyAsync(&r, c.red_out.p, sizeof(double), cudaMemcpyDeviceToHost, c.s()), "dot d2h");
   cuda_check(cudaStreamSynchronize(c.s()), "dot sync");
   return r;
+}
+
+void dev_dot2(Ctx& c, const double* x1, const double* y1, const double* x2, const double* y2, long n, double* r1,
+              double* r2) {
+  *r1 = *r2 = 0.0;
+  if (n <= 0) return;
+  unsigned int* tk = dot_ticket(c);
+  launch_dot_fused(x1, y1, x2, y2, n, c.red_out.d(), c.red.d(), tk, c.s());
+  c.st.kernel_launches++;
+  double r[2] = {0, 0};
+  cuda_check(cudaMemcpyAsync(r, c.red_out.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.s()), "dot d2h");
+  cuda_check(cudaStreamSynchronize(c.s()), "dot sync");
+  *r1 = r[0];
+  *r2 = r[1];
+}
+
+void dev_project(Ctx& c, const double* u, double* v, long n) {
+  if (n <= 0) return;
+  unsigned int* tk = dot_ticket(c);
+  double* a = c.red_out.d() + 8;   // consumed by the next launch on the stream
+  launch_dot_fused(u, v, nullptr, nullptr, n, a, c.red.d(), tk, c.s());
+  launch_axpy_dev(n, a, -1.0, u, v, c.s());
+  c.st.kernel_launches += 2;
 }
 
 static GemmTask gemm(const double* A, const double* B, double* C, int m, int n, int k, int lda, int ldb, int ldc,
@@ -354,6 +386,25 @@ void boundary_envs(Ctx& c, Family& F) {
     cuda_check(cudaStreamSynchronize(c.s()), "boundary env sync");
     E.valid = true;
   }
+}
+
+std::vector<uint16_t> fused_piece_masks(const Mpo& W, int p, bool left) {
+  const MpoBond& b = W.bond[left ? p + 1 : p];
+  std::vector<uint16_t> m((size_t)b.n, 0);
+  for (const auto& e : W.site[p].e) m[left ? e.w1 : e.w0] |= (uint16_t)(1u << (4 * e.so + e.si));
+  return m;
+}
+
+int piece_dim(const Fused& F, int f, int s) {
+  for (const auto& p : F.pc[f])
+    if (p.s == s || p.s < 0) return p.dim;
+  return 0;
+}
+
+int piece_off(const Fused& F, int f, int s) {
+  for (const auto& p : F.pc[f])
+    if (p.s == s || p.s < 0) return p.off;
+  return 0;
 }
 
 static std::vector<int> class_list(const MpoBond& b) {
@@ -825,7 +876,38 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
   P.xin.release();
   P.xin.alloc(&c, std::max(P.nk, 1L) * sizeof(double));
   std::vector<GemmTask> t1, t2;
+  // Algorithmic flops: a channel's fused block is non-zero only on the local
+  // pieces (s_out, s_in) its site tensor reaches, so both phases count the
+  // block products piece by piece (the dense GEMMs below also multiply the
+  // zero pieces; the tensor-core path skips them).
+  const Mpo& W = *P.fam->mpo;
+  const std::vector<uint16_t> mL = fused_piece_masks(W, lf.p, true);
+  const std::vector<uint16_t> mR = rf.ext ? std::vector<uint16_t>() : fused_piece_masks(W, rf.p, false);
+  auto piece_flops = [](const Fused& Fb, int fb, const Fused& Fk, int fk, uint16_t mask, double other) {
+    double f = 0;
+    for (int b = 0; b < 16; ++b)
+      if (mask >> b & 1) f += 2.0 * piece_dim(Fb, fb, b >> 2) * piece_dim(Fk, fk, b & 3) * other;
+    return f;
+  };
   double fl = 0;
+  for (const auto& S : rf.stk) {
+    const int fb = rf.kb[S.bidx], fk = rf.kk[S.kidx];
+    const double dl = lf.FLk.d[lf.kk[S.kidx]];
+    if (rf.ext) {
+      fl += 2.0 * S.nw * (double)rf.FRb.d[fb] * rf.FRk.d[fk] * dl;
+      continue;
+    }
+    const int c0 = W.bond[rf.p].class_start[S.cls];
+    for (int w = 0; w < S.nw; ++w) fl += piece_flops(rf.FRb, fb, rf.FRk, fk, mR[c0 + w], dl);
+  }
+  for (size_t bi = 0; bi < P.mid_b.size(); ++bi) {
+    const int fb = lf.kb[bi];
+    const double dr = rf.FRb.d[rf.kb[bi]];
+    for (const auto& sg : lf.seg[bi]) {
+      const int c0 = W.bond[lf.p + 1].class_start[sg.cls], fk = lf.kk[sg.kidx];
+      for (int w = 0; w < sg.nw; ++w) fl += piece_flops(lf.FLb, fb, lf.FLk, fk, mL[c0 + w], dr);
+    }
+  }
   for (const auto& S : rf.stk) {
     int ki = S.kidx, bi = S.bidx;
     const LeftFused::Seg* sg = lf.find_seg(bi, S.cls);
@@ -834,7 +916,6 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
     int dFLk = lf.FLk.d[lf.kk[ki]];
     t1.push_back(gemm(rf.base() + S.off, P.xin.d() + P.off_k[ki], P.tt.d() + P.tt_off[bi] + sg->koff, dFRb, dFLk,
                       dFRk, dFRk, dFRk, (int)lf.K[bi], GEMM_TB, S.nw, (long long)dFRb * dFRk, 0, sg->width));
-    fl += 2.0 * S.nw * (double)dFRb * dFLk * dFRk;
   }
   long long base_tiles = 0;
   for (size_t bi = 0; bi < P.mid_b.size(); ++bi) {
@@ -883,7 +964,6 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
     t.ksplit = ksv[bi];
     t.sK = segs[bi].sstride;
     t2.push_back(t);
-    fl += 2.0 * (double)dFLb * dFRb * K;
   }
   P.nseg = (int)segs.size();
   P.seg_tiles = plan_split_tiles(segs.data(), P.nseg);

@@ -302,7 +302,7 @@ struct Ctx {
   }
 
   // scratch
-  DBuf red, red_out, gtask, ctask;
+  DBuf red, red_out, red_ticket, gtask, ctask;
   DBuf eig_work, eig_w, eig_info;
   static constexpr int NEIG = 8;   // concurrent eigensolver streams
   cudaStream_t eig_stream[NEIG] = {};
@@ -349,6 +349,11 @@ void validate_gemm(const Ctx& c, const GemmTask& t);
 void validate_copy(const Ctx& c, const CopyTask& t);
 void run_copies(Ctx& c, std::vector<CopyTask>& t);
 double dev_dot(Ctx& c, const double* x, const double* y, long n);
+// x1.y1 and x2.y2 in one pass (one launch, one host round trip)
+void dev_dot2(Ctx& c, const double* x1, const double* y1, const double* x2, const double* y2, long n, double* r1,
+              double* r2);
+// v -= (u.v) u with the coefficient kept on the device (no host round trip)
+void dev_project(Ctx& c, const double* u, double* v, long n);
 
 void ensure_lf(Ctx& c, MPS& m, int p);
 void ensure_rf(Ctx& c, MPS& m, int p);
@@ -365,6 +370,15 @@ void make_right_fused(Ctx& c, Family& F, int p, const std::vector<QN>& kb, const
                       RightFused& rf);
 void env_update_left(Ctx& c, Family& F, int p, const LeftFused& lf);
 void env_update_right(Ctx& c, Family& F, int p, const RightFused& rf);
+
+// Local pieces (s_out, s_in) of the fused operators of site p that can be
+// non-zero, per target channel: bit 4 s_out + s_in of entry w, w a channel of
+// MPO bond p+1 for the left side (L'), of bond p for the right side (R').
+std::vector<uint16_t> fused_piece_masks(const Mpo& W, int p, bool left);
+// Dimension of the piece of local state s in sector f of a fused space (0 if
+// the sector has none); a piece of state -1 (a bare bond sector) matches any s.
+int piece_dim(const Fused& F, int f, int s);
+int piece_off(const Fused& F, int f, int s);
 
 void two_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long>& off, long& n);
 void one_site_middle(const MPS& m, int l, std::vector<QN>& mid, std::vector<long>& off, long& n);

@@ -163,13 +163,52 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
-__global__ void dot_partial(const double* __restrict__ x, const double* __restrict__ y, long n,
-                            double* __restrict__ part) {
-  double s = 0.0;
+// Dots of one or two vector pairs in one launch.  Every block stores its
+// partial sums; the block that finishes last (a ticket counter) adds the
+// partials in block order, so the value does not depend on timing and equals
+// a reduction of the partials by one block per output.
+__global__ void dot_fused(const double* __restrict__ x1, const double* __restrict__ y1,
+                          const double* __restrict__ x2, const double* __restrict__ y2, long n,
+                          double* __restrict__ part, unsigned int* ticket, double* __restrict__ out) {
+  const bool two = x2 != nullptr;
+  double s1 = 0.0, s2 = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    s1 = fma(x1[i], y1[i], s1);
+    if (two) s2 = fma(x2[i], y2[i], s2);
+  }
+  s1 = block_sum(s1);
+  if (two) s2 = block_sum(s2);
+  __shared__ unsigned int tk;
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s1;
+    if (two) part[gridDim.x + blockIdx.x] = s2;
+    __threadfence();
+    tk = atomicAdd(ticket, 1u);
+  }
+  __syncthreads();
+  if (tk != gridDim.x - 1) return;
+  __threadfence();
+  const volatile double* vp = part;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    a += vp[i];
+    if (two) b += vp[gridDim.x + i];
+  }
+  a = block_sum(a);
+  if (two) b = block_sum(b);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    if (two) out[1] = b;
+    *ticket = 0u;
+  }
+}
+
+// y += sgn * (*a) x with the coefficient read on the device (no host round trip)
+__global__ void axpy_dev_kernel(long n, const double* __restrict__ a, double sgn, const double* __restrict__ x,
+                                double* __restrict__ y) {
+  const double cf = sgn * *a;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    s = fma(x[i], y[i], s);
-  s = block_sum(s);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
+    y[i] = fma(cf, x[i], y[i]);
 }
 
 __global__ void multidot_partial(const double* __restrict__ V, long ld, const double* __restrict__ x,
@@ -330,9 +369,13 @@ void launch_copy_f64(const CopyTask* d_tasks, int ntasks, long long total, cudaS
   copy_f64_kernel<<<grid, 256, 0, s>>>(d_tasks, ntasks, total);
 }
 
-void launch_dot(const double* x, const double* y, long n, double* d_out, double* d_part, cudaStream_t s) {
-  dot_partial<<<RED_BLOCKS, RED_T, 0, s>>>(x, y, n, d_part);
-  reduce_partials<<<1, RED_T, 0, s>>>(d_part, RED_BLOCKS, d_out);
+void launch_dot_fused(const double* x1, const double* y1, const double* x2, const double* y2, long n, double* d_out,
+                      double* d_part, unsigned int* d_ticket, cudaStream_t s) {
+  dot_fused<<<RED_BLOCKS, RED_T, 0, s>>>(x1, y1, x2, y2, n, d_part, d_ticket, d_out);
+}
+
+void launch_axpy_dev(long n, const double* d_a, double sgn, const double* x, double* y, cudaStream_t s) {
+  axpy_dev_kernel<<<elem_grid(n), 256, 0, s>>>(n, d_a, sgn, x, y);
 }
 
 void launch_multidot(long n, int m, const double* V, long ld, const double* x, double* d_out, double* d_part,

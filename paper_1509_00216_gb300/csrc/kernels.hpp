@@ -50,7 +50,12 @@ void launch_gemm_f64(const GemmTask* d_tasks, int ntasks, long long total_tiles,
 void launch_copy_f64(const CopyTask* d_tasks, int ntasks, long long total_tiles, cudaStream_t s);
 
 // BLAS-1 on FP64 device vectors.  Reductions write into a device scalar.
-void launch_dot(const double* x, const double* y, long n, double* d_out, double* d_partial, cudaStream_t s);
+// x1.y1 (and x2.y2 when x2 is not null) in one launch into d_out[0] (and
+// d_out[1]); d_partial holds 2 x 512 doubles, d_ticket one zeroed counter
+// (left zeroed)
+void launch_dot_fused(const double* x1, const double* y1, const double* x2, const double* y2, long n, double* d_out,
+                      double* d_partial, unsigned int* d_ticket, cudaStream_t s);
+void launch_axpy_dev(long n, const double* d_a, double sgn, const double* x, double* y, cudaStream_t s);  // y += sgn*(*d_a) x
 void launch_axpy(long n, double a, const double* x, double* y, cudaStream_t s);   // y += a x
 void launch_axpby(long n, double a, const double* x, double b, double* y, cudaStream_t s);  // y = a x + b y
 void launch_scale(long n, double a, double* x, cudaStream_t s);

@@ -197,8 +197,7 @@ double davidson(Ctx& c, SigmaPlan& P, double* x, long n, const double* diag, dou
 // Q v = v - u (u.v)  (u normalised, or null)
 void project(Ctx& c, const double* u, double* v, long n) {
   if (!u) return;
-  double a = dev_dot(c, u, v, n);
-  launch_axpy(n, -a, u, v, c.s());
+  dev_project(c, u, v, n);
 }
 
 struct LinOp {
@@ -247,8 +246,9 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
   };
   precond(r.d(), z.d());
   copyv(c, p.d(), z.d(), n);
-  double rz = dev_dot(c, r.d(), z.d(), n);
-  double rn = vnorm(c, r);
+  double rz = 0, rr = 0;
+  dev_dot2(c, r.d(), z.d(), r.d(), r.d(), n, &rz, &rr);
+  double rn = std::sqrt(std::max(0.0, rr));
   int it = 0;
   *indefinite = false;
   while (rn > thr && it < maxit) {
@@ -263,10 +263,11 @@ double solve_linear(Ctx& c, LinOp& A, const double* b, double* x, const double* 
     launch_axpy(n, alpha, p.d(), x, c.s());
     launch_axpy(n, -alpha, Ap.d(), r.d(), c.s());
     precond(r.d(), z.d());
-    double rz2 = dev_dot(c, r.d(), z.d(), n);
+    double rz2 = 0;
+    dev_dot2(c, r.d(), z.d(), r.d(), r.d(), n, &rz2, &rr);
     launch_axpby(n, 1.0, z.d(), rz2 / rz, p.d(), c.s());
     rz = rz2;
-    rn = vnorm(c, r);
+    rn = std::sqrt(std::max(0.0, rr));
     if (!std::isfinite(rn)) throw Error(ST_NUMERIC, "non-finite residual in the local CG solve");
     ++it;
   }
@@ -902,9 +903,19 @@ double lcc_local(Ctx& c, MPS& target, SigmaPlan& P11, SigmaPlan& P10, MPS& tket,
   // orthogonal to Phi0.  Projecting v out when |v| < 1 would remove a
   // legitimate direction of the local space (P v is not Phi0) and make the
   // sweeps non-variational.
+  // "Lies in the range" is decided at the accuracy v is computed with: in
+  // FP64 (products and environments) a deficit 1 - |v|^2/<Phi0|Phi0> below
+  // 1e-9; with tensor-core products or environments (about 2^-24 relative)
+  // below 1e-5, a hundred times that error and below the inverse condition
+  // number that the split-BF16 refinement still resolves.  A deficit d under
+  // the threshold is projected: the direction dropped, (Phi0 - P v), lies
+  // outside the range of P, so the Hylleraas value it could still gain is
+  // bounded by the part of the right-hand side outside that range.
+  const bool all64 = prec == MPSLCC_FP64 && rprec == MPSLCC_FP64 && c.gemm_prec == MPSLCC_FP64;
+  const double deficit = all64 ? 1e-9 : 1e-5;
   double vn = std::sqrt(std::max(0.0, dev_dot(c, ub.d(), ub.d(), n)));
   const double* u = nullptr;
-  if (vn > 1e-10 && vn * vn >= (1.0 - 1e-9) * n00) {
+  if (vn > 1e-10 && vn * vn >= (1.0 - deficit) * n00) {
     launch_scale(n, 1.0 / vn, ub.d(), c.s());
     u = ub.d();
   }

@@ -54,6 +54,11 @@ struct alignas(64) TcTask {
   long long cbatch;     // output offset between batch entries (elements)
   long long kstride;    // output offset between K-split partials (elements);
                         // each split stores its own partial (mode 2)
+  const int* kr;        // K runs, or null for K steps at 0, KT, 2 KT, ...: nkr + 1
+                        // pairs {first K column, steps before the run} (the last
+                        // pair a sentinel holding the task's step count), then
+                        // per K split the run its first step lies in
+  int nkr;
 };
 
 namespace {
@@ -472,11 +477,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
         const int nk = min(T->ksteps, kt0 + T->kchunk) - kt0;
         const int row0 = tc.tmi * 128, col0 = tc.tni * T->ntile;
         const uint32_t bbytes = (uint32_t)T->ntile * 128u;
+        // K runs: the open run (first column rx, steps rs0 .. rs1 - 1) and
+        // the next one's entries, loaded a run ahead
+        const int* kr = T->kr;
+        int r = 0, rx = 0, rs0 = 0, rs1 = 0x7fffffff, nx = 0, ns1 = 0;
+        if (kr) {
+          r = __ldg(kr + 2 * (T->nkr + 1) + tc.ks);
+          rx = __ldg(kr + 2 * r);
+          rs0 = __ldg(kr + 2 * r + 1);
+          rs1 = __ldg(kr + 2 * r + 3);
+          if (r + 1 < T->nkr) { nx = __ldg(kr + 2 * r + 2); ns1 = __ldg(kr + 2 * r + 5); }
+        }
         for (int j = 0; j < nk; ++j, ++it) {
           const uint32_t s = it % NST, ph = (it / NST) & 1u;
           if (!mbar_wait(&empty[s], ph ^ 1u, err, 1, wait_ns)) { *s_abort = 1; break; }
           uint8_t* st = smem + s * SB;
-          const int kx = (kt0 + j) * KT;
+          const int g = kt0 + j;
+          int kx = g * KT;
+          if (kr) {
+            if (g >= rs1) {   // steps of one split are consecutive: the next run
+              ++r;
+              rx = nx;
+              rs0 = rs1;
+              rs1 = ns1;
+              if (r + 1 < T->nkr) { nx = __ldg(kr + 2 * r + 2); ns1 = __ldg(kr + 2 * r + 5); }
+            }
+            kx = rx + (g - rs0) * KT;
+          }
           mbar_expect_tx(&full[s], (SPLIT ? 2u : 1u) * (A_BYTES + bbytes));
           tma_load(st, &T->ma, &full[s], kx, row0, tc.b, T->a3d);
           tma_load(st + A_BYTES, &T->mb, &full[s], kx, col0, tc.b, T->b3d);
@@ -744,18 +771,19 @@ int sm_count(Ctx& c) { return sm_count_dev(c.device); }
 // batch > 1 it holds `batch` products of this shape: operand X advances by
 // x_bs elements per entry (0 = shared by all entries) and C by c_bs.
 // Number of K splits a task gets for a requested count: every split non-empty.
-int tc_ksplit(int prec, int k, int hint) {
-  const int KT = prec == MPSLCC_TF32 ? 32 : 64;
-  const int ksteps = (k + KT - 1) / KT;
+int tc_ksplit_steps(int ksteps, int hint) {
   int ks = std::max(1, std::min(hint, ksteps));
   const int kchunk = (ksteps + ks - 1) / ks;
   return (ksteps + kchunk - 1) / kchunk;
 }
 
+
 TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long ldb, int m, int n, int k, void* C,
                  int ldc, int rpb, long long bstride, int mode, int ksplit_hint, long long soff = 0,
                  long lo_off = 0, int batch = 1, long long a_bs = 0, long long b_bs = 0, long long c_bs = 0,
-                 long long kstride = 0, int cap = 256) {
+                 long long kstride = 0, int cap = 256, int steps = 0) {
+  // steps > 0: the task reads `steps` K steps through a run table set by the
+  // caller (k is then the operands' K extent, not the summed length)
   TcTask t;
   std::memset(&t, 0, sizeof(t));
   const int KT = prec == MPSLCC_TF32 ? 32 : 64;
@@ -786,11 +814,11 @@ TcTask make_task(Ctx& c, int prec, const void* A, long lda, const void* B, long 
   t.n = n;
   t.k = k;
   t.mode = mode;
-  t.ksteps = (k + KT - 1) / KT;
+  t.ksteps = steps > 0 ? steps : (k + KT - 1) / KT;
   t.ksplit = std::max(1, std::min(ksplit_hint, t.ksteps));
   t.kchunk = (t.ksteps + t.ksplit - 1) / t.ksplit;
   t.ksplit = (t.ksteps + t.kchunk - 1) / t.kchunk;  // every split non-empty
-  MPSLCC_REQUIRE(t.ksplit == tc_ksplit(prec, k, ksplit_hint), ST_INTERNAL, "K split count");
+  MPSLCC_REQUIRE(t.ksplit == tc_ksplit_steps(t.ksteps, ksplit_hint), ST_INTERNAL, "K split count");
   MPSLCC_REQUIRE(t.ksplit == 1 || mode == 0 || (mode == 2 && kstride > 0), ST_INTERNAL,
                  "split-K partials need atomic adds or a partial stride");
   t.kstride = t.ksplit > 1 ? kstride : 0;
@@ -912,13 +940,25 @@ struct TcState {
   std::vector<long> stk_off;
   std::vector<std::vector<long>> koff8;   // per bra key: channel-block offsets in the padded K
   std::vector<ConvTask> xconv;
+  // Phase-1 units: the rows of one R' stack with bra local state so (piece
+  // of dimension d at row boff of the bra sector) for channels w0 .. w1-1
+  // whose pieces (so, .) agree; `in` = the ket local states of those pieces.
+  // The low-precision stack keeps its rows so-major (all channels' rows of
+  // one so contiguous), so a unit's rows are contiguous from row0.
+  struct Unit1 { int si, so, d, boff, w0, w1, in; long row0; };
+  std::vector<Unit1> u1;
+  // Phase-2 units: the rows of middle sector bi with bra local state so.
+  struct Unit2 { int bi, so, d, boff; };
+  std::vector<Unit2> u2;
+  std::vector<uint16_t> mL;               // piece masks of L' channels (MPO bond l+1)
+  std::vector<int> cstartL;               // class starts of that bond
   // Task lists per sigma variant v ([0] the layout's own precision: TF32,
   // BF16 or BF16X3; [1] BF16X6, six-block layout only) and N-tile cap
   // (TC_CAPS), built on first use; phase 2 keeps its K-split FP32 partials
   // and the segments of their fixed-order sum.
   struct Lists {
     bool built = false;
-    DBuf t1, t2, ypart, segs;
+    DBuf t1, t2, ypart, segs, runs;
     int n1 = 0, n2 = 0, nseg = 0;
     long long tiles1 = 0, tiles2 = 0, seg_tiles = 0;
   };
@@ -942,6 +982,10 @@ SigmaPlan::~SigmaPlan() { tc_release(*this); }
 // of BF16X6 (error about 2^-24 relative, at the level of the FP32
 // accumulation); blocks 0 and 2 alone are the hi / lo pair of BF16X3
 // (hi*hi + hi*lo + lo*hi, about 2^-17).
+//
+// Only the local pieces (s_out, s_in) that a channel's site tensor reaches
+// are converted (the rest of a fused block is zero and stays zero in the
+// copies), and the task lists read only those pieces (K runs, below).
 void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   const int layout = (prec == MPSLCC_BF16X3 || prec == MPSLCC_BF16X6) ? MPSLCC_BF16X3 : prec;
   TcState*& slot = layout == MPSLCC_BF16X3 ? P.tc6 : P.tc;
@@ -957,7 +1001,11 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   const int sp = six ? 6 : 1;
   const LeftFused& lf = P.lf;
   const RightFused& rf = P.rf;
+  const Mpo& W = *P.fam->mpo;
   const size_t nbk = P.mid_b.size(), nkk = P.mid_k.size();
+  S->mL = fused_piece_masks(W, lf.p, true);
+  S->cstartL = W.bond[lf.p + 1].class_start;
+  const std::vector<uint16_t> mR = rf.ext ? std::vector<uint16_t>() : fused_piece_masks(W, rf.p, false);
   // padded K layout per bra key: each channel block width rounded up to 8
   S->K8.assign(nbk, 0);
   S->lcat_off.assign(nbk, 0);
@@ -976,12 +1024,38 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     lsz += pad8((long)lf.FLb.d[lf.kb[bi]] * sp * K8);
     tsz += pad8((long)rf.FRb.d[rf.kb[bi]] * sp * K8);
   }
+  // phase-1 units and the so-major row layout of the low-precision stacks;
+  // a one-site position's right side (an environment) is one piece per sector
+  const int nso = rf.ext ? 1 : 4;
   S->stk_off.assign(rf.stk.size(), 0);
   long ssz = 0;
   for (size_t si = 0; si < rf.stk.size(); ++si) {
     const auto& st = rf.stk[si];
+    const int fb = rf.kb[st.bidx];
+    const int c0 = rf.ext ? 0 : W.bond[rf.p].class_start[st.cls];
     S->stk_off[si] = ssz;
-    ssz += pad8((long)st.nw * rf.FRb.d[rf.kb[st.bidx]] * sp * pad8(rf.FRk.d[rf.kk[st.kidx]]));
+    long row = 0;
+    for (int so = 0; so < nso; ++so) {
+      const int d = piece_dim(rf.FRb, fb, so);
+      if (d == 0) continue;
+      const int boff = piece_off(rf.FRb, fb, so);
+      for (int w = 0; w < st.nw;) {
+        const int in = rf.ext ? 1 : (mR[c0 + w] >> (4 * so)) & 15;
+        int w1 = w + 1;
+        while (w1 < st.nw && (rf.ext ? 1 : (mR[c0 + w1] >> (4 * so)) & 15) == in) ++w1;
+        if (in) S->u1.push_back({(int)si, so, d, boff, w, w1, in, row + (long)w * d});
+        w = w1;
+      }
+      row += (long)st.nw * d;
+    }
+    ssz += pad8(row * sp * pad8(rf.FRk.d[rf.kk[st.kidx]]));
+  }
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    const int fb = lf.kb[bi];
+    for (int so = 0; so < 4; ++so) {
+      const int d = piece_dim(lf.FLb, fb, so);
+      if (d > 0) S->u2.push_back({(int)bi, so, d, piece_off(lf.FLb, fb, so)});
+    }
   }
   S->x_off.assign(nkk, 0);
   long xsz = 0;
@@ -998,44 +1072,64 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   zalloc(S->tt, tsz, es);
   zalloc(S->x, xsz, es);
   zalloc(S->err, 4, 1);
-  // FP64 -> low precision copies of L' (A side of phase 2) and R' (A side of
-  // phase 1)
+  // FP64 -> low precision copies of the non-zero pieces of L' (A side of
+  // phase 2), per run of channels with equal piece masks
   std::vector<ConvTask> cv;
-  for (size_t bi = 0; bi < nbk; ++bi) {
-    int rows = lf.FLb.d[lf.kb[bi]];
-    for (size_t g = 0; g < lf.seg[bi].size(); ++g) {
-      const auto& sg = lf.seg[bi][g];
-      ConvTask t;
-      std::memset(&t, 0, sizeof(t));
-      t.src = lf.data.d() + lf.off[bi] + sg.koff;
-      t.dst = (char*)S->lcat.p + (size_t)(S->lcat_off[bi] + koff8[bi][g]) * es;
-      t.rows = rows;
-      t.cols = sg.width;
-      t.src_ld = (int)lf.K[bi];
-      t.dst_ld = (int)(sp * S->K8[bi]);
-      t.batch = sg.nw;
-      t.s_src = sg.width;
-      t.s_dst = pad8(sg.width);
-      t.pattern = six ? 2 : 0;
-      t.soff = S->K8[bi];
-      cv.push_back(t);
-    }
-  }
-  for (size_t si = 0; si < rf.stk.size(); ++si) {
-    const auto& st = rf.stk[si];
-    int rb = rf.FRb.d[rf.kb[st.bidx]], rk = rf.FRk.d[rf.kk[st.kidx]];
+  auto conv = [&](const double* src, int src_ld, void* dst, int dst_ld, int rows, int cols, int batch,
+                  long long s_src, long long s_dst, long long soff) {
     ConvTask t;
     std::memset(&t, 0, sizeof(t));
-    t.src = rf.base() + st.off;
-    t.dst = (char*)S->rstk.p + (size_t)S->stk_off[si] * es;
-    t.rows = st.nw * rb;
-    t.cols = rk;
-    t.src_ld = rk;
-    t.dst_ld = (int)(sp * pad8(rk));
-    t.batch = 1;
+    t.src = src;
+    t.dst = dst;
+    t.rows = rows;
+    t.cols = cols;
+    t.src_ld = src_ld;
+    t.dst_ld = dst_ld;
+    t.batch = batch;
+    t.s_src = s_src;
+    t.s_dst = s_dst;
     t.pattern = six ? 2 : 0;
-    t.soff = pad8(rk);
+    t.soff = soff;
     cv.push_back(t);
+  };
+  for (size_t bi = 0; bi < nbk; ++bi) {
+    const int fb = lf.kb[bi];
+    const long K = lf.K[bi], pitch = sp * S->K8[bi];
+    for (size_t g = 0; g < lf.seg[bi].size(); ++g) {
+      const auto& sg = lf.seg[bi][g];
+      const int fk = lf.kk[sg.kidx], c0 = S->cstartL[sg.cls];
+      for (int w = 0; w < sg.nw;) {
+        const uint16_t m = S->mL[c0 + w];
+        int w1 = w + 1;
+        while (w1 < sg.nw && S->mL[c0 + w1] == m) ++w1;
+        for (int b = 0; b < 16; ++b) {
+          if (!(m >> b & 1)) continue;
+          const int so = b >> 2, sn = b & 3;
+          const int dr = piece_dim(lf.FLb, fb, so), dc = piece_dim(lf.FLk, fk, sn);
+          if (dr == 0 || dc == 0) continue;
+          const long ro = piece_off(lf.FLb, fb, so), co = piece_off(lf.FLk, fk, sn);
+          conv(lf.data.d() + lf.off[bi] + ro * K + sg.koff + (long)w * sg.width + co, (int)K,
+               (char*)S->lcat.p + (size_t)(S->lcat_off[bi] + ro * pitch + koff8[bi][g] + (long)w * pad8(sg.width) + co) * es,
+               (int)pitch, dr, dc, w1 - w, sg.width, pad8(sg.width), S->K8[bi]);
+        }
+        w = w1;
+      }
+    }
+  }
+  // ... and of R' (A side of phase 1), into the so-major stack rows
+  for (const auto& u : S->u1) {
+    const auto& st = rf.stk[u.si];
+    const int rb = rf.FRb.d[rf.kb[st.bidx]], fk = rf.kk[st.kidx], rk = rf.FRk.d[fk];
+    const long pitch = sp * pad8(rk);
+    for (int sn = 0; sn < 4; ++sn) {
+      if (!(u.in >> sn & 1)) continue;
+      const int dc = piece_dim(rf.FRk, fk, sn);
+      if (dc == 0) continue;
+      const long co = piece_off(rf.FRk, fk, sn);
+      conv(rf.base() + st.off + ((long)u.w0 * rb + u.boff) * rk + co, rk,
+           (char*)S->rstk.p + (size_t)(S->stk_off[u.si] + u.row0 * pitch + co) * es, (int)pitch, u.d, dc, u.w1 - u.w0,
+           (long long)rb * rk, (long long)u.d * pitch, pad8(rk));
+    }
   }
   run_conv(c, layout, cv, S->conv);
   // per-call conversion of the input vector (B side of phase 1)
@@ -1055,19 +1149,49 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     S->xconv.push_back(t);
   }
   S->koff8 = koff8;
-  // algorithmic bytes of each variant: operands read once and results
-  // written once, per BF16 (or TF32) piece read or written
+  // algorithmic bytes of each variant, per BF16 (or TF32) piece read or
+  // written: the non-zero pieces of the fused operators and the parts of the
+  // vector and of T they multiply, each read once; T and sigma written once
+  std::vector<double> a1(rf.stk.size(), 0.0);
+  std::vector<int> inu(rf.stk.size(), 0);
+  for (const auto& u : S->u1) {
+    const int fk = rf.kk[rf.stk[u.si].kidx];
+    for (int sn = 0; sn < 4; ++sn)
+      if (u.in >> sn & 1) a1[u.si] += (double)(u.w1 - u.w0) * u.d * piece_dim(rf.FRk, fk, sn);
+    inu[u.si] |= u.in;
+  }
   for (int v = 0; v < (six ? 2 : 1); ++v) {
     const int pcs = v == 1 ? 6 : (six ? 2 : 1);
     for (size_t si = 0; si < rf.stk.size(); ++si) {
       const auto& st = rf.stk[si];
-      const double rb = rf.FRb.d[rf.kb[st.bidx]], rk = rf.FRk.d[rf.kk[st.kidx]], lk = lf.FLk.d[lf.kk[st.kidx]];
-      S->bytes1[v] += (double)es * pcs * (st.nw * rb * rk + lk * rk + st.nw * rb * lk);
+      const int fk = rf.kk[st.kidx];
+      const double rb = rf.FRb.d[rf.kb[st.bidx]], lk = lf.FLk.d[lf.kk[st.kidx]];
+      double xk = 0;
+      for (int sn = 0; sn < 4; ++sn)
+        if (inu[si] >> sn & 1) xk += piece_dim(rf.FRk, fk, sn);
+      if (rf.ext) xk = rf.FRk.d[fk];
+      S->bytes1[v] += (double)es * pcs * (a1[si] + lk * xk + st.nw * rb * lk);
     }
     for (size_t bi = 0; bi < nbk; ++bi) {
       if (S->K8[bi] == 0) continue;
-      const double lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
-      S->bytes2[v] += (double)es * pcs * (lb * S->K8[bi] + rb * S->K8[bi]) + 4.0 * lb * rb;
+      const int fb = lf.kb[bi];
+      const double lb = lf.FLb.d[fb], rb = rf.FRb.d[rf.kb[bi]];
+      double a = 0, kc = 0;
+      for (const auto& sg : lf.seg[bi]) {
+        const int fk = lf.kk[sg.kidx], c0 = S->cstartL[sg.cls];
+        for (int w = 0; w < sg.nw; ++w) {
+          const uint16_t m = S->mL[c0 + w];
+          int used = 0;
+          for (int b = 0; b < 16; ++b)
+            if (m >> b & 1) {
+              a += (double)piece_dim(lf.FLb, fb, b >> 2) * piece_dim(lf.FLk, fk, b & 3);
+              used |= 1 << (b & 3);
+            }
+          for (int sn = 0; sn < 4; ++sn)
+            if (used >> sn & 1) kc += piece_dim(lf.FLk, fk, sn);
+        }
+      }
+      S->bytes2[v] += (double)es * pcs * (a + rb * kc) + 4.0 * lb * rb;
     }
   }
   cuda_check(cudaStreamSynchronize(c.s()), "tc prepare sync");
@@ -1076,6 +1200,60 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
 namespace {
 
 constexpr int TC_CAPS[3] = {256, 128, 64};
+
+// K runs of one task: its non-zero columns come as ranges [a, b) of the
+// operands' K extent; each run starts on an 8-element boundary (16-byte TMA
+// coordinate) and is read in whole steps of KT columns.  A range that starts
+// before the open run's last step ends joins that run, so no column is read
+// by two runs; the columns a run reads outside its ranges are zero in the
+// operand whose zero pieces were skipped, so they add nothing.
+struct KRun { long kx, steps; };
+std::vector<KRun> merge_runs(std::vector<std::pair<long, long>>& r, int KT) {
+  std::sort(r.begin(), r.end());
+  std::vector<KRun> out;
+  long de = 0;
+  for (const auto& x : r) {
+    if (x.second <= x.first) continue;
+    const long a8 = x.first & ~7L;
+    if (!out.empty() && a8 < out.back().kx + out.back().steps * KT) {
+      de = std::max(de, x.second);
+      out.back().steps = (de - out.back().kx + KT - 1) / KT;
+    } else {
+      out.push_back({a8, (x.second - a8 + KT - 1) / KT});
+      de = x.second;
+    }
+  }
+  return out;
+}
+
+// Appends a task's run table (pairs {kx, steps before}, a sentinel, then the
+// run of each K split's first step) to `tab`; returns its offset.
+long append_runs(std::vector<int>& tab, const std::vector<KRun>& runs, int kchunk, int ksplit) {
+  const long at = (long)tab.size();
+  long s0 = 0;
+  for (const auto& r : runs) {
+    MPSLCC_REQUIRE(r.kx >= 0 && r.kx < (1L << 30) && s0 < (1L << 30), ST_INTERNAL, "K run out of range");
+    tab.push_back((int)r.kx);
+    tab.push_back((int)s0);
+    s0 += r.steps;
+  }
+  tab.push_back(0);
+  tab.push_back((int)s0);
+  size_t ri = 0;
+  long acc = 0;
+  for (int ks = 0; ks < ksplit; ++ks) {
+    const long first = (long)ks * kchunk;
+    while (ri + 1 < runs.size() && acc + runs[ri].steps <= first) acc += runs[ri++].steps;
+    tab.push_back((int)ri);
+  }
+  return at;
+}
+
+long total_steps(const std::vector<KRun>& r) {
+  long s = 0;
+  for (const auto& x : r) s += x.steps;
+  return s;
+}
 
 // Task lists of sigma variant v with N tiles of at most TC_CAPS[ci] rows.
 void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
@@ -1091,77 +1269,136 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
   const size_t nbk = P.mid_b.size();
   const long long target = 2LL * sm_count(c);
   // v = 0: the layout's own precision; v = 1: BF16X6 (plain BF16 kernel over
-  // all six blocks)
+  // all six blocks, so every run repeats in each block)
   const int kp = v == 1 ? MPSLCC_BF16 : layout;
+  const int KT = kp == MPSLCC_TF32 ? 32 : 64;
+  const int reps = v == 1 ? 6 : 1;
   std::vector<TcTask> t1, t2;
-  // phase 1: T_w^T = R'_w psi^T for all channels of a class in one tall GEMM
+  std::vector<std::vector<KRun>> r1, r2;
+  // phase 1: T_w^T = R'_w psi^T, one task per unit (rows of one bra local
+  // state for a run of channels of one class); K runs = the ket pieces the
+  // unit's channels reach
   const int mode1 = v == 1 ? 5 : (six ? 3 : (layout == MPSLCC_TF32 ? 2 : 1));
-  for (size_t si = 0; si < rf.stk.size(); ++si) {
-    const auto& st = rf.stk[si];
-    int bi = st.bidx, ki = st.kidx;
+  for (const auto& u : S->u1) {
+    const auto& st = rf.stk[u.si];
+    const int bi = st.bidx, ki = st.kidx;
     const LeftFused::Seg* sg = lf.find_seg(bi, st.cls);
-    size_t g = sg - lf.seg[bi].data();
-    int rb = rf.FRb.d[rf.kb[bi]], rk = rf.FRk.d[rf.kk[ki]], lk = lf.FLk.d[lf.kk[ki]];
+    const size_t g = sg - lf.seg[bi].data();
+    const int fk = rf.kk[ki], rk = rf.FRk.d[fk], lk = lf.FLk.d[lf.kk[ki]];
     const long pitch = sp * pad8(rk);
     const int kk = v == 1 ? (int)pitch : rk;
-    void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + S->koff8[bi][g]) * es;
+    std::vector<std::pair<long, long>> rg;
+    for (int j = 0; j < reps; ++j)
+      for (int sn = 0; sn < 4; ++sn) {
+        if (!(u.in >> sn & 1)) continue;
+        const long co = piece_off(rf.FRk, fk, sn) + (long)j * pad8(rk);
+        rg.push_back({co, co + piece_dim(rf.FRk, fk, sn)});
+      }
+    std::vector<KRun> runs = merge_runs(rg, KT);
+    const int steps = (int)total_steps(runs);
+    if (steps == 0) continue;   // the ket sector has none of the unit's pieces: T stays zero there
+    r1.push_back(std::move(runs));
+    const long ldc = sp * S->K8[bi];
+    void* C = (char*)S->tt.p +
+              (size_t)(S->tt_off[bi] + S->koff8[bi][g] + (long)u.w0 * pad8(lk) + (long)u.boff * ldc) * es;
     // split tasks: lo parts in block 2 of both operands (and of the output)
     const long long so = v == 1 ? S->K8[bi] : 2 * S->K8[bi];
-    t1.push_back(make_task(c, kp, (char*)S->rstk.p + (size_t)S->stk_off[si] * es, pitch,
-                           (char*)S->x.p + (size_t)S->x_off[ki] * es, pitch, st.nw * rb, lk, kk, C,
-                           (int)(sp * S->K8[bi]), rb, pad8(lk), mode1, 1, six ? so : 0, six ? 2 * pad8(rk) : 0, 1,
-                           0, 0, 0, 0, cap));
+    t1.push_back(make_task(c, kp, (char*)S->rstk.p + (size_t)(S->stk_off[u.si] + u.row0 * pitch) * es, pitch,
+                           (char*)S->x.p + (size_t)S->x_off[ki] * es, pitch, (u.w1 - u.w0) * u.d, lk, kk, C, (int)ldc,
+                           u.d, pad8(lk), mode1, 1, six ? so : 0, six ? 2 * pad8(rk) : 0, 1, 0, 0, 0, 0, cap,
+                           steps));
   }
-  // phase 2: sigma = Lcat Tt^T, split over K so that every tile carries
-  // about the same number of K steps (a balanced persistent schedule).  The
-  // split counts come from an N tiling of 256 whatever the launch's cap, so
-  // every cap stores the same partials.  Split j of a middle sector stores
-  // its FP32 partial at its own offset; one reduction sums the partials in
-  // increasing j into the FP64 sigma, so the result does not depend on the
-  // order the splits finish in.
+  // phase 2: sigma = Lcat Tt^T per unit (rows of one bra local state of a
+  // middle sector), over the K runs of the channel pieces those rows reach,
+  // split over K so that every tile carries about the same number of K steps
+  // (a balanced persistent schedule).  The split counts come from an N tiling
+  // of 256 whatever the launch's cap, so every cap stores the same partials.
+  // Split j of a unit stores its FP32 partial at its own offset; one
+  // reduction sums the partials in increasing j into the FP64 sigma, so the
+  // result does not depend on the order the splits finish in.
+  for (const auto& u : S->u2) {
+    std::vector<std::pair<long, long>> rg;
+    const int bi = u.bi;
+    for (int j = 0; j < reps; ++j)
+      for (size_t g = 0; g < lf.seg[bi].size(); ++g) {
+        const auto& sg = lf.seg[bi][g];
+        const int fk = lf.kk[sg.kidx], c0 = S->cstartL[sg.cls];
+        for (int w = 0; w < sg.nw; ++w) {
+          const int row = (S->mL[c0 + w] >> (4 * u.so)) & 15;
+          for (int sn = 0; sn < 4; ++sn) {
+            if (!(row >> sn & 1)) continue;
+            const long co = (long)j * S->K8[bi] + S->koff8[bi][g] + (long)w * pad8(sg.width) + piece_off(lf.FLk, fk, sn);
+            rg.push_back({co, co + piece_dim(lf.FLk, fk, sn)});
+          }
+        }
+      }
+    r2.push_back(merge_runs(rg, KT));
+  }
   long long work = 0;
-  for (size_t bi = 0; bi < nbk; ++bi) {
-    if (S->K8[bi] == 0) continue;
-    const int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
-    const long kk = v == 1 ? sp * S->K8[bi] : S->K8[bi];
+  for (size_t i = 0; i < S->u2.size(); ++i) {
+    const int rb = rf.FRb.d[rf.kb[S->u2[i].bi]];
     const long nt = std::min<long>(256, (rb + 15) / 16 * 16);
-    work += (long long)((lb + 127) / 128) * ((rb + nt - 1) / nt) * ((kk + 63) / 64);
+    work += (long long)((S->u2[i].d + 127) / 128) * ((rb + nt - 1) / nt) * total_steps(r2[i]);
   }
   const long long kper = std::max(4LL, (work + 4 * target - 1) / (4 * target));
   std::vector<SplitSeg> segs;
-  std::vector<int> ksv(nbk, 0);
+  std::vector<int> ksv(S->u2.size(), 0);
   long poff = 0;
-  for (size_t bi = 0; bi < nbk; ++bi) {
-    const int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
+  for (size_t i = 0; i < S->u2.size(); ++i) {
+    const auto& u = S->u2[i];
+    const int rb = rf.FRb.d[rf.kb[u.bi]];
     SplitSeg sg;
     std::memset(&sg, 0, sizeof(sg));
-    sg.out_off = P.off_b[bi];
-    sg.m = lb;
+    sg.out_off = P.off_b[u.bi] + (long long)u.boff * rb;
+    sg.m = u.d;
     sg.n = rb;
     sg.ldp = (int)((rb + 3) / 4 * 4);   // 16-byte aligned partial rows
-    sg.sstride = (long long)lb * sg.ldp;
-    if (S->K8[bi] > 0) {
-      const long pitch = sp * S->K8[bi];
-      const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
-      const int hint = (int)std::max(1LL, (((long long)kk + 63) / 64 + kper - 1) / kper);
-      ksv[bi] = tc_ksplit(kp, kk, hint);
-      sg.nsplit = ksv[bi];
+    sg.sstride = (long long)u.d * sg.ldp;
+    const long steps = total_steps(r2[i]);
+    if (steps > 0) {
+      const int hint = (int)std::max(1LL, (steps + kper - 1) / kper);
+      ksv[i] = tc_ksplit_steps((int)steps, hint);
+      sg.nsplit = ksv[i];
       sg.part_off = poff;
-      poff += (long)ksv[bi] * sg.sstride;
+      poff += (long)ksv[i] * sg.sstride;
     }
-    segs.push_back(sg);   // nsplit = 0: no channel reaches the sector, sigma is zero there
+    segs.push_back(sg);   // nsplit = 0: no channel reaches these rows, sigma is zero there
   }
   Ls.ypart.alloc(&c, std::max<long>(poff, 4) * 4);
-  for (size_t bi = 0; bi < nbk; ++bi) {
-    if (S->K8[bi] == 0) continue;
-    int lb = lf.FLb.d[lf.kb[bi]], rb = rf.FRb.d[rf.kb[bi]];
-    const long pitch = sp * S->K8[bi];
-    const int kk = v == 1 ? (int)pitch : (int)S->K8[bi];
-    const SplitSeg& sg = segs[bi];
-    t2.push_back(make_task(c, kp, (char*)S->lcat.p + (size_t)S->lcat_off[bi] * es, pitch,
-                           (char*)S->tt.p + (size_t)S->tt_off[bi] * es, pitch, lb, rb, kk,
-                           (float*)Ls.ypart.p + sg.part_off, sg.ldp, 1 << 30, 0, 2, ksv[bi], 0,
-                           (six && v == 0) ? 2 * S->K8[bi] : 0, 1, 0, 0, 0, sg.sstride, cap));
+  std::vector<int> r2i;
+  for (size_t i = 0; i < S->u2.size(); ++i) {
+    if (ksv[i] == 0) continue;
+    const auto& u = S->u2[i];
+    const int rb = rf.FRb.d[rf.kb[u.bi]];
+    const long pitch = sp * S->K8[u.bi];
+    const int kk = v == 1 ? (int)pitch : (int)S->K8[u.bi];
+    const SplitSeg& sg = segs[i];
+    t2.push_back(make_task(c, kp, (char*)S->lcat.p + (size_t)(S->lcat_off[u.bi] + (long)u.boff * pitch) * es, pitch,
+                           (char*)S->tt.p + (size_t)S->tt_off[u.bi] * es, pitch, u.d, rb, kk,
+                           (float*)Ls.ypart.p + sg.part_off, sg.ldp, 1 << 30, 0, 2, ksv[i], 0,
+                           (six && v == 0) ? 2 * S->K8[u.bi] : 0, 1, 0, 0, 0, sg.sstride, cap,
+                           (int)total_steps(r2[i])));
+    r2i.push_back((int)i);
+  }
+  // run tables of both phases in one device buffer
+  std::vector<int> tab;
+  std::vector<long> at1(t1.size()), at2(t2.size());
+  for (size_t i = 0; i < t1.size(); ++i) {
+    MPSLCC_REQUIRE(t1[i].ksplit == 1, ST_INTERNAL, "phase-1 task split over K");
+    at1[i] = append_runs(tab, r1[i], t1[i].kchunk, t1[i].ksplit);
+  }
+  for (size_t i = 0; i < t2.size(); ++i) at2[i] = append_runs(tab, r2[r2i[i]], t2[i].kchunk, t2[i].ksplit);
+  Ls.runs.alloc(&c, std::max<size_t>(tab.size(), 4) * sizeof(int));
+  if (!tab.empty())
+    cuda_check(cudaMemcpyAsync(Ls.runs.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, c.s()),
+               "K runs");
+  for (size_t i = 0; i < t1.size(); ++i) {
+    t1[i].kr = (const int*)Ls.runs.p + at1[i];
+    t1[i].nkr = (int)r1[i].size();
+  }
+  for (size_t i = 0; i < t2.size(); ++i) {
+    t2[i].kr = (const int*)Ls.runs.p + at2[i];
+    t2[i].nkr = (int)r2[r2i[i]].size();
   }
   Ls.nseg = (int)segs.size();
   Ls.seg_tiles = plan_split_tiles(segs.data(), (int)segs.size());
@@ -1181,6 +1418,7 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
   if (!t2.empty())
     cuda_check(cudaMemcpyAsync(Ls.t2.p, t2.data(), t2.size() * sizeof(TcTask), cudaMemcpyHostToDevice, c.s()),
                "tc tasks");
+  cuda_check(cudaStreamSynchronize(c.s()), "tc lists sync");
   Ls.built = true;
 }
 
