@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the mixed-vs-FP64 comparison on a window of middle positions")
     ap.add_argument("--compare-window", type=int, default=4)
+    ap.add_argument("--eig-reserved-sms", type=int, default=0,
+                    help="SMs left to the truncation's eigensolvers while fused operators are built (0: library default)")
     ap.add_argument("--verbose", type=int, default=0,
                     help="library verbosity (2: per-truncation stage times on stderr)")
     ap.add_argument("--partition", default=None,
@@ -70,6 +72,11 @@ def parse():
     ap.add_argument("--profile-sigma", type=int, default=0,
                     help="profiling mode: N sigma products at the middle position inside NVTX range 'sigma'")
     return ap.parse_args()
+
+
+# DRAM traffic per algorithmic byte of sigma phases 1 and 2 (split BF16),
+# measured by ncu on the kernel as it stands (see the roofline block)
+TRAFFIC_RATIO = (2.00, 1.19)
 
 
 def peaks():
@@ -355,6 +362,7 @@ def gpu_arm(args, rank, world, local_rank):
     M1 = args.M1 or c["M1"]
     prec = PREC[args.prec]
     ctx = mp.Context(device=local_rank, prec=prec, tol=1e-8, max_iter=60, torch_memory=True, verbose=args.verbose,
+                     eig_reserved_sms=args.eig_reserved_sms,
                      init_guess=1 if args.dmrg_init == "product" else 0)
     ctx.build_mpo(c["h"], c["V"], c["n_alpha"] + c["n_beta"], 0)
     ctx.set_spaces(c["n_core"], c["n_active"])
@@ -462,9 +470,17 @@ def gpu_arm(args, rank, world, local_rank):
                 "tensor_tflops": flops / tcs / 1e12 if tcs else None,
                 "tensor_frac_of_bf16_sustained": flops / tcs / 1e12 / pk["bf16_sust"] if tcs else None}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["achieved"] else None
-    # DRAM bytes of the counted launches come from an ncu capture of the
-    # kernel as it stands; none is taken inside this run
-    roof["traffic"] = None
+    # DRAM bytes (read + write) per algorithmic byte of each sigma phase, from
+    # an ncu capture (--set full) of the kernel as it stands: both phases of
+    # one split-BF16 sigma at the middle position of the 3-band chain at
+    # M1 = 1000, a case small enough to capture.  The bench size has the same
+    # task, run and tile structure, so its traffic is scaled by the
+    # algorithmic bytes; none is measured inside this run.
+    if prec == 3 and tc["n"]:
+        roof["traffic"] = (TRAFFIC_RATIO[0] * tc["b1"] + TRAFFIC_RATIO[1] * tc["b2"]) / launches
+        roof["traffic_source"] = "scaled from the ncu capture at M1 = 1000 (DRAM/algorithmic %.2f, %.2f)" % TRAFFIC_RATIO
+    else:
+        roof["traffic"] = None
     roof["peak_source"] = pk["src"]
     value = world * flops / dev_s / 1e12
     line = dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,

@@ -114,6 +114,11 @@ typedef struct {
                             phases: 1 (default) tries N tiles of 256, 128 and
                             64 rows on the first products of each position
                             and keeps the fastest; 0 uses 256              */
+  int eig_reserved_sms;  /* SMs that the persistent tensor-core launches
+                            leave free while a truncation's FP64
+                            eigensolvers run on their side streams (the
+                            next position's fused operators are built
+                            meanwhile): 0 = default (32), < 0 = none       */
 } mpslcc_opts;
 
 typedef struct {

@@ -46,7 +46,7 @@ class Opts(C.Structure):
                 ("refine_steps", C.c_int), ("seed", C.c_ulonglong), ("verbose", C.c_int),
                 ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p),
                 ("init_guess", C.c_int), ("wait_timeout_s", C.c_double), ("tc_environments", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("eig_reserved_sms", C.c_int)]
 
 
 class Energies(C.Structure):
@@ -162,7 +162,7 @@ class Context:
 
     def __init__(self, device=0, prec=FP64, tol=1e-10, max_iter=200, seed=7, verbose=0, refine_steps=4,
                  davidson_max_subspace=24, torch_memory=False, init_guess=0, wait_timeout_s=0.0, alloc=None,
-                 stream=None, tc_environments=False, autotune=True):
+                 stream=None, tc_environments=False, autotune=True, eig_reserved_sms=0):
         L = lib()
         o = Opts()
         L.mpslcc_default_opts(C.byref(o))
@@ -178,6 +178,7 @@ class Context:
         o.wait_timeout_s = wait_timeout_s
         o.tc_environments = 1 if tc_environments else 0
         o.autotune = 1 if autotune else 0
+        o.eig_reserved_sms = int(eig_reserved_sms)
         if stream is not None:
             o.stream = C.c_void_p(stream)
         self._cb = None

@@ -161,7 +161,7 @@ mpslcc_status mpslcc_destroy(mpslcc_ctx* ctx) {
     c.phin.clear();
     c.ofam.clear();
     for (auto& b : c.boxes) b.release();
-    for (DBuf* b : {&c.red, &c.red_out, &c.gtask, &c.ctask, &c.eig_work, &c.eig_w, &c.eig_info, &c.scratch_a,
+    for (DBuf* b : {&c.red, &c.red_out, &c.red_ticket, &c.gtask, &c.ctask, &c.eig_work, &c.eig_w, &c.eig_info, &c.scratch_a,
                     &c.scratch_b, &c.scratch_tc, &c.tc_conv_tasks, &c.tc_gemm_tasks, &c.tc_err})
       b->release();
     for (int s = 0; s < Ctx::NEIG; ++s) c.eig_ws[s].release();
@@ -175,7 +175,10 @@ mpslcc_status mpslcc_destroy(mpslcc_ctx* ctx) {
     if (c.solver) cusolverDnDestroy(c.solver);
     for (cudaEvent_t e : {c.ev0, c.ev1, c.ev_p0, c.ev_p1, c.ev_p2})
       if (e) cudaEventDestroy(e);
-    if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+    if (c.own_stream && c.stream) {
+      cudaStreamDestroy(c.stream);
+      c.stream = nullptr;   // a buffer released after this point is freed synchronously
+    }
   }
   delete ctx;
   return MPSLCC_OK;

@@ -87,7 +87,8 @@ void DBuf::release() {
   if (p && c) c->allocs.erase((uintptr_t)p);
   if (p && c) {
     if (c->opts.free) c->opts.free(p, bytes, c->opts.alloc_user);
-    else cudaFreeAsync(p, c->stream);
+    else if (c->stream || !c->own_stream) cudaFreeAsync(p, c->stream);
+    else cudaFree(p);   // the context's own stream is gone (teardown): a synchronous free
   }
   p = nullptr;
   bytes = 0;
@@ -873,13 +874,16 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
   }
   P.tt.release();
   P.tt.alloc(&c, std::max(tts, 1L) * sizeof(double));
+  // phase 1 writes only the rows of T that a channel's R' reaches; the rest
+  // stay zero for every product of the plan
+  cuda_check(cudaMemsetAsync(P.tt.p, 0, std::max(tts, 1L) * sizeof(double), c.s()), "T zero");
   P.xin.release();
   P.xin.alloc(&c, std::max(P.nk, 1L) * sizeof(double));
   std::vector<GemmTask> t1, t2;
   // Algorithmic flops: a channel's fused block is non-zero only on the local
   // pieces (s_out, s_in) its site tensor reaches, so both phases count the
-  // block products piece by piece (the dense GEMMs below also multiply the
-  // zero pieces; the tensor-core path skips them).
+  // block products piece by piece (and both the FP64 and the tensor-core
+  // tasks multiply only those pieces).
   const Mpo& W = *P.fam->mpo;
   const std::vector<uint16_t> mL = fused_piece_masks(W, lf.p, true);
   const std::vector<uint16_t> mR = rf.ext ? std::vector<uint16_t>() : fused_piece_masks(W, rf.p, false);
@@ -908,45 +912,127 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
       for (int w = 0; w < sg.nw; ++w) fl += piece_flops(lf.FLb, fb, lf.FLk, fk, mL[c0 + w], dr);
     }
   }
+  // Phase 1: T_w^T = R'_w psi^T per unit — the rows of one R' stack with bra
+  // local state so for a run of channels whose pieces (so, .) agree, batched
+  // over those channels — summing only over the ket pieces the unit reaches
+  // (K runs).  A one-site position's right side is one piece per sector.
+  // Every task's run table is {operand column, virtual start} pairs and a
+  // sentinel; a task whose runs cover its K extent densely has none.
+  std::vector<std::vector<int>> rt1, rt2;
+  auto add_runs = [](std::vector<std::pair<int, int>>& rg, int kext, std::vector<int>& tab) {
+    std::sort(rg.begin(), rg.end());
+    std::vector<std::pair<int, int>> m;   // merged [start, end)
+    for (const auto& x : rg) {
+      if (x.second <= x.first) continue;
+      if (!m.empty() && x.first <= m.back().second) m.back().second = std::max(m.back().second, x.second);
+      else m.push_back(x);
+    }
+    tab.clear();
+    int v = 0;
+    for (const auto& x : m) {
+      MPSLCC_REQUIRE(x.first >= 0 && x.second <= kext, ST_INTERNAL, "K run outside the operand");
+      tab.push_back(x.first);
+      tab.push_back(v);
+      v += x.second - x.first;
+    }
+    tab.push_back(0);
+    tab.push_back(v);
+    return v;
+  };
+  const int nso = rf.ext ? 1 : 4;
   for (const auto& S : rf.stk) {
-    int ki = S.kidx, bi = S.bidx;
+    const int ki = S.kidx, bi = S.bidx;
     const LeftFused::Seg* sg = lf.find_seg(bi, S.cls);
     MPSLCC_REQUIRE(sg && sg->kidx == ki, ST_INTERNAL, "sigma plan: segment/stack mismatch");
-    int dFRk = rf.FRk.d[rf.kk[ki]], dFRb = rf.FRb.d[rf.kb[bi]];
-    int dFLk = lf.FLk.d[lf.kk[ki]];
-    t1.push_back(gemm(rf.base() + S.off, P.xin.d() + P.off_k[ki], P.tt.d() + P.tt_off[bi] + sg->koff, dFRb, dFLk,
-                      dFRk, dFRk, dFRk, (int)lf.K[bi], GEMM_TB, S.nw, (long long)dFRb * dFRk, 0, sg->width));
+    const int fb = rf.kb[bi], fk = rf.kk[ki];
+    const int dFRk = rf.FRk.d[fk], dFRb = rf.FRb.d[fb], dFLk = lf.FLk.d[lf.kk[ki]];
+    const long K = lf.K[bi];
+    const int c0 = rf.ext ? 0 : W.bond[rf.p].class_start[S.cls];
+    for (int so = 0; so < nso; ++so) {
+      const int d = piece_dim(rf.FRb, fb, so);
+      if (d == 0) continue;
+      const int boff = piece_off(rf.FRb, fb, so);
+      for (int w = 0; w < S.nw;) {
+        const int in = rf.ext ? 1 : (mR[c0 + w] >> (4 * so)) & 15;
+        int w1 = w + 1;
+        while (w1 < S.nw && (rf.ext ? 1 : (mR[c0 + w1] >> (4 * so)) & 15) == in) ++w1;
+        if (in) {
+          std::vector<std::pair<int, int>> rg;
+          for (int sn = 0; sn < 4; ++sn)
+            if (in >> sn & 1) {
+              const int o = piece_off(rf.FRk, fk, sn);
+              rg.push_back({o, o + piece_dim(rf.FRk, fk, sn)});
+            }
+          std::vector<int> tab;
+          const int kv = add_runs(rg, dFRk, tab);
+          if (kv > 0) {
+            GemmTask t = gemm(rf.base() + S.off + ((long)w * dFRb + boff) * dFRk, P.xin.d() + P.off_k[ki],
+                              P.tt.d() + P.tt_off[bi] + (long)boff * K + sg->koff + (long)w * sg->width, d, dFLk, dFRk,
+                              dFRk, dFRk, (int)K, GEMM_TB, w1 - w, (long long)dFRb * dFRk, 0, sg->width);
+            if (!(tab.size() == 4 && tab[0] == 0 && kv == dFRk)) {
+              t.kv = kv;
+              t.nkr = (int)tab.size() / 2 - 1;
+              rt1.push_back(std::move(tab));
+            } else {
+              rt1.push_back({});
+            }
+            t1.push_back(t);
+          }
+        }
+        w = w1;
+      }
+    }
   }
+  // phase 2: sigma rows of one (middle sector, bra local state) = Lcat Tt^T
+  // over the K runs of the L' pieces those rows reach, split over K when the
+  // row blocks alone give too few tiles.  Every split stores its partial at
+  // its own offset of `ypart`; sigma_apply sums them in a fixed order (no
+  // atomics: results are reproducible bit for bit)
+  struct U2 { int bi, so, d, boff, kv; std::vector<int> tab; };
+  std::vector<U2> u2;
   long long base_tiles = 0;
   for (size_t bi = 0; bi < P.mid_b.size(); ++bi) {
-    int dFLb = lf.FLb.d[lf.kb[bi]], dFRb = rf.FRb.d[rf.kb[bi]];
-    base_tiles += (long long)((dFLb + 63) / 64) * ((dFRb + 63) / 64);
+    const int fb = lf.kb[bi], dFRb = rf.FRb.d[rf.kb[bi]];
+    for (int so = 0; so < 4; ++so) {
+      const int d = piece_dim(lf.FLb, fb, so);
+      if (d == 0) continue;
+      std::vector<std::pair<int, int>> rg;
+      for (const auto& sg : lf.seg[bi]) {
+        const int c0 = W.bond[lf.p + 1].class_start[sg.cls], fk = lf.kk[sg.kidx];
+        for (int w = 0; w < sg.nw; ++w)
+          for (int sn = 0; sn < 4; ++sn)
+            if ((mL[c0 + w] >> (4 * so + sn)) & 1) {
+              const int o = (int)(sg.koff + (long)w * sg.width + piece_off(lf.FLk, fk, sn));
+              rg.push_back({o, o + piece_dim(lf.FLk, fk, sn)});
+            }
+      }
+      U2 u{(int)bi, so, d, piece_off(lf.FLb, fb, so), 0, {}};
+      u.kv = add_runs(rg, (int)lf.K[bi], u.tab);
+      base_tiles += (long long)((d + 63) / 64) * ((dFRb + 63) / 64);
+      u2.push_back(std::move(u));
+    }
   }
-  // phase 2: one GEMM per middle sector with the channel sum in K, split over
-  // K when the sectors alone give too few tiles.  Every split stores its
-  // partial at its own offset of `ypart`; sigma_apply sums them in a fixed
-  // order (no atomics: results are reproducible bit for bit)
   const long long target = 152LL * 6;
   std::vector<SplitSeg> segs;
-  std::vector<int> ksv(P.mid_b.size(), 0);
+  std::vector<int> ksv(u2.size(), 0);
   long poff = 0;
-  for (size_t bi = 0; bi < P.mid_b.size(); ++bi) {
-    long K = lf.K[bi];
-    int dFLb = lf.FLb.d[lf.kb[bi]], dFRb = rf.FRb.d[rf.kb[bi]];
+  for (size_t i = 0; i < u2.size(); ++i) {
+    const U2& u = u2[i];
+    const int dFRb = rf.FRb.d[rf.kb[u.bi]];
     SplitSeg sg;
     std::memset(&sg, 0, sizeof(sg));
-    sg.out_off = P.off_b[bi];
-    sg.m = dFLb;
+    sg.out_off = P.off_b[u.bi] + (long long)u.boff * dFRb;
+    sg.m = u.d;
     sg.n = dFRb;
     sg.ldp = dFRb;
-    sg.sstride = (long long)dFLb * dFRb;
-    if (K > 0) {  // K = 0: no operator channel reaches this output sector, it stays zero
+    sg.sstride = (long long)u.d * dFRb;
+    if (u.kv > 0) {  // no run: no operator channel reaches these rows, they stay zero
       int ks = 1;
       if (base_tiles < target) {
         long long f = (target + base_tiles - 1) / std::max(1LL, base_tiles);
-        ks = (int)std::max(1LL, std::min(f, (long long)(K / 256)));
+        ks = (int)std::max(1LL, std::min(f, (long long)(u.kv / 256)));
       }
-      ksv[bi] = ks;
+      ksv[i] = ks;
       sg.nsplit = ks;
       sg.part_off = poff;
       poff += (long)ks * sg.sstride;
@@ -955,16 +1041,34 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
   }
   P.ypart.release();
   P.ypart.alloc(&c, std::max(poff, 1L) * sizeof(double));
-  for (size_t bi = 0; bi < P.mid_b.size(); ++bi) {
-    if (ksv[bi] == 0) continue;
-    long K = lf.K[bi];
-    int dFLb = lf.FLb.d[lf.kb[bi]], dFRb = rf.FRb.d[rf.kb[bi]];
-    GemmTask t = gemm(lf.data.d() + lf.off[bi], P.tt.d() + P.tt_off[bi], P.ypart.d() + segs[bi].part_off, dFLb, dFRb,
-                      (int)K, (int)K, (int)K, dFRb, GEMM_TB);
-    t.ksplit = ksv[bi];
-    t.sK = segs[bi].sstride;
+  for (size_t i = 0; i < u2.size(); ++i) {
+    if (ksv[i] == 0) continue;
+    U2& u = u2[i];
+    const long K = lf.K[u.bi];
+    const int dFRb = rf.FRb.d[rf.kb[u.bi]];
+    GemmTask t = gemm(lf.data.d() + lf.off[u.bi] + (long)u.boff * K, P.tt.d() + P.tt_off[u.bi],
+                      P.ypart.d() + segs[i].part_off, u.d, dFRb, (int)K, (int)K, (int)K, dFRb, GEMM_TB);
+    t.ksplit = ksv[i];
+    t.sK = segs[i].sstride;
+    t.kv = u.kv;
+    t.nkr = (int)u.tab.size() / 2 - 1;
+    rt2.push_back(std::move(u.tab));
     t2.push_back(t);
   }
+  // run tables of both phases in one device buffer
+  std::vector<int> tab;
+  std::vector<long> at1(t1.size(), -1), at2(t2.size(), -1);
+  for (size_t i = 0; i < t1.size(); ++i)
+    if (!rt1[i].empty()) { at1[i] = (long)tab.size(); tab.insert(tab.end(), rt1[i].begin(), rt1[i].end()); }
+  for (size_t i = 0; i < t2.size(); ++i) { at2[i] = (long)tab.size(); tab.insert(tab.end(), rt2[i].begin(), rt2[i].end()); }
+  P.kruns.release();
+  P.kruns.alloc(&c, std::max<size_t>(tab.size(), 4) * sizeof(int));
+  if (!tab.empty())
+    cuda_check(cudaMemcpyAsync(P.kruns.p, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice, c.s()),
+               "upload K runs");
+  for (size_t i = 0; i < t1.size(); ++i)
+    if (at1[i] >= 0) t1[i].kr = (const int*)P.kruns.p + at1[i];
+  for (size_t i = 0; i < t2.size(); ++i) t2[i].kr = (const int*)P.kruns.p + at2[i];
   P.nseg = (int)segs.size();
   P.seg_tiles = plan_split_tiles(segs.data(), P.nseg);
   P.segs.release();

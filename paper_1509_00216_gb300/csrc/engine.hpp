@@ -182,6 +182,7 @@ struct SigmaPlan {
   // FP64 phase 2: per-split partial products and the segments of their
   // fixed-order sum into sigma
   DBuf ypart, segs;
+  DBuf kruns;                          // K-run tables of the FP64 tasks
   int nseg = 0;
   long long seg_tiles = 0;
   double flops = 0.0;                  // algorithmic flops of one application
@@ -314,6 +315,9 @@ struct Ctx {
   // precision of the per-site FP64 GEMM tasks (fusion, renormalisation,
   // truncation): MPSLCC_FP64, or MPSLCC_BF16X3 inside mixed-precision sweeps
   int gemm_prec = MPSLCC_FP64;
+  // SMs the persistent tensor-core launches leave free (set while a
+  // truncation's eigensolvers run on their side streams)
+  int tc_sm_reserve = 0;
 
   // tile-shape autotuner of the sigma phases (tc_gemm.cu): best N-tile cap
   // per (bra, ket, operator, position, phase, sigma precision)

@@ -43,49 +43,79 @@ __global__ void __launch_bounds__(GT) gemm_f64_kernel(const GemmTask* __restrict
     const double* B = T.B + (long long)b * T.sB;
     double* C = T.C + (long long)b * T.sC;
     const bool ta = T.flags & GEMM_TA, tb = T.flags & GEMM_TB;
-    int kchunk = (T.k + T.ksplit - 1) / T.ksplit;
+    const int kv = T.kr ? T.kv : T.k;   // summed K length
+    int kchunk = (kv + T.ksplit - 1) / T.ksplit;
     kchunk = ((kchunk + BK - 1) / BK) * BK;
     const int k0 = ks * kchunk;
-    const int k1 = min(T.k, k0 + kchunk);
+    const int k1 = min(kv, k0 + kchunk);
     const int row0 = tm * BM, col0 = tn * BN;
     double acc[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    for (int kk = k0; kk < k1; kk += BK) {
-      for (int e = threadIdx.x; e < BM * BK; e += GT) {
-        int i, q;
-        if (!ta) { i = e / BK; q = e - i * BK; }
-        else { q = e / BM; i = e - q * BM; }
-        const int gi = row0 + i, gk = kk + q;
-        double v = 0.0;
-        if (gi < T.m && gk < k1) v = ta ? A[(long long)gk * T.lda + gi] : A[(long long)gi * T.lda + gk];
-        As[q][i] = v;
+    // the operand column spans [ps, pe) to sum over: [k0, k1) itself, or the
+    // parts of the K runs that overlap virtual [k0, k1) (the first found by
+    // binary search)
+    int run = 0;
+    if (T.kr) {
+      int lo = 0, hi = T.nkr - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (T.kr[2 * mid + 1] <= k0) lo = mid;
+        else hi = mid - 1;
       }
-      for (int e = threadIdx.x; e < BN * BK; e += GT) {
-        int j, q;
-        if (!tb) { q = e / BN; j = e - q * BN; }
-        else { j = e / BK; q = e - j * BK; }
-        const int gj = col0 + j, gk = kk + q;
-        double v = 0.0;
-        if (gj < T.n && gk < k1) v = tb ? B[(long long)gj * T.ldb + gk] : B[(long long)gk * T.ldb + gj];
-        Bs[q][j] = v;
+      run = lo;
+    }
+    for (bool first = true;; first = false) {
+      int ps, pe;
+      if (!T.kr) {
+        if (!first) break;
+        ps = k0;
+        pe = k1;
+      } else {
+        if (run >= T.nkr) break;
+        const int v0 = T.kr[2 * run + 1], v1 = T.kr[2 * run + 3];
+        if (v0 >= k1) break;
+        const int vb = max(v0, k0), ve = min(v1, k1);
+        ps = T.kr[2 * run] + (vb - v0);
+        pe = T.kr[2 * run] + (ve - v0);
+        ++run;
       }
-      __syncthreads();
+      for (int kk = ps; kk < pe; kk += BK) {
+        for (int e = threadIdx.x; e < BM * BK; e += GT) {
+          int i, q;
+          if (!ta) { i = e / BK; q = e - i * BK; }
+          else { q = e / BM; i = e - q * BM; }
+          const int gi = row0 + i, gk = kk + q;
+          double v = 0.0;
+          if (gi < T.m && gk < pe) v = ta ? A[(long long)gk * T.lda + gi] : A[(long long)gi * T.lda + gk];
+          As[q][i] = v;
+        }
+        for (int e = threadIdx.x; e < BN * BK; e += GT) {
+          int j, q;
+          if (!tb) { q = e / BN; j = e - q * BN; }
+          else { j = e / BK; q = e - j * BK; }
+          const int gj = col0 + j, gk = kk + q;
+          double v = 0.0;
+          if (gj < T.n && gk < pe) v = tb ? B[(long long)gj * T.ldb + gk] : B[(long long)gk * T.ldb + gj];
+          Bs[q][j] = v;
+        }
+        __syncthreads();
 #pragma unroll
-      for (int q = 0; q < BK; ++q) {
-        double a[4], bv[4];
+        for (int q = 0; q < BK; ++q) {
+          double a[4], bv[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = As[q][ty + 16 * i];
+          for (int i = 0; i < 4; ++i) a[i] = As[q][ty + 16 * i];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[q][tx + 16 * j];
+          for (int j = 0; j < 4; ++j) bv[j] = Bs[q][tx + 16 * j];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {

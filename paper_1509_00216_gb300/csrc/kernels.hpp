@@ -27,6 +27,12 @@ struct GemmTask {
   int tm, tn;     // tile counts (filled by plan_gemm_tiles)
   long long tile0;
   long long sK;   // element stride between split-K partials (0 = atomic adds)
+  // K runs (optional): the product sums over kv virtual K indices, run r
+  // covering virtual [kr[2r+1], kr[2r+3]) at operand columns (rows, for a
+  // transposed operand) from kr[2r]; nkr runs and a sentinel {0, kv}.  k is
+  // then the operands' K extent (bounds checks), kv the summed length.
+  const int* kr;
+  int nkr, kv;
 };
 enum { GEMM_TA = 1, GEMM_TB = 2 };
 

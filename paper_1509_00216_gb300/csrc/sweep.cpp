@@ -775,7 +775,7 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
   // one half-sweep of two-site Davidson updates (Eq. EH): products and the
   // Davidson tolerance in `prec`; `noise` > 0 perturbs each two-site state
   // before truncation by that amplitude (per unit-norm vector)
-  auto half_sweep = [&](bool right, int prec, double noise, unsigned long long tag) {
+  auto half_sweep = [&](bool right, int prec, double noise, unsigned long long tag, int M) {
     for (int step = 0; step <= k - 2; ++step) {
       int l = right ? step : k - 2 - step;
       SigmaPlan P;
@@ -795,7 +795,7 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
       if (noise > 0)
         launch_noise(n, noise / std::sqrt((double)std::max(n, 1L)), tag * 1000003ull + (unsigned long long)l, x.d(),
                      c.s());
-      double disc = truncate(c, c.phi0, l, x.d(), M0, right);
+      double disc = truncate(c, c.phi0, l, x.d(), M, right);
       c.max_disc = std::max(c.max_disc, disc);
       invalidate_site(c.f00, l);
       invalidate_site(c.f00, l + 1);
@@ -807,17 +807,24 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
     }
   };
   const int sprec = mixed ? MPSLCC_BF16X3 : MPSLCC_FP64;
-  {
-    // mixed precision: every per-site product on the tensor cores (split BF16)
-    GemmPrec gp(c, sprec);
-    bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
-    for (int sw = 0; sw < n_sweeps; ++sw) {
-      // decaying perturbation so that early sweeps keep states outside the
-      // current local optimum; the last sweep is noise-free
-      const double amp = sw < n_sweeps - 1 ? 1e-3 * std::pow(0.1, sw) : 0.0;
-      for (int dir = 0; dir < 2; ++dir)
-        half_sweep(dir == 0, sprec, amp, c.opts.seed * 7919ull + (unsigned long long)(2 * sw + dir));
-    }
+  // In mixed precision the first two (exploratory, most perturbed) sweeps run
+  // in FP64 at a bond dimension of at most 128: which local optimum the
+  // reference ends in is decided there, so it does not depend on the
+  // rounding of the tensor-core products, and FP64 at that size costs a
+  // small fraction of one sweep at M0.
+  const int n_explore = mixed && n_sweeps >= 3 ? 2 : 0;
+  const int M_explore = std::min(M0, 128);
+  for (int sw = 0; sw < n_sweeps; ++sw) {
+    const bool explore = sw < n_explore;
+    const int p = explore ? MPSLCC_FP64 : sprec;
+    GemmPrec gp(c, p);
+    if (sw == 0 || sw == n_explore) bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);   // environments in `p`
+    // decaying perturbation so that early sweeps keep states outside the
+    // current local optimum; the last sweep is noise-free
+    const double amp = sw < n_sweeps - 1 ? 1e-3 * std::pow(0.1, sw) : 0.0;
+    for (int dir = 0; dir < 2; ++dir)
+      half_sweep(dir == 0, p, amp, c.opts.seed * 7919ull + (unsigned long long)(2 * sw + dir),
+                 explore ? M_explore : M0);
   }
   if (mixed) {
     // FP64 sweep: the split-BF16 Davidson stops at a residual of ~1e-4, an
@@ -827,8 +834,8 @@ double dmrg_reference(Ctx& c, int M0, int n_sweeps) {
     // FP64 accuracy
     GemmPrec gp(c, MPSLCC_FP64);
     bind(c, c.f00, &c.phi0, MPO_H0, &c.phi0);
-    half_sweep(true, MPSLCC_FP64, 0.0, 0);
-    half_sweep(false, MPSLCC_FP64, 0.0, 0);
+    half_sweep(true, MPSLCC_FP64, 0.0, 0, M0);
+    half_sweep(false, MPSLCC_FP64, 0.0, 0, M0);
   }
   c.E0 = E;
   c.have_E0 = true;
@@ -1117,6 +1124,17 @@ struct LccRun {
       FusedAhead* ah = ahead.data();
       if (next >= 0)
         nextf = [this, ah, fams, next, right]() {
+          // the persistent tensor-core launches (one CTA per SM) leave some
+          // SMs to the eigensolvers' kernels on the side streams
+          struct Reserve {
+            Ctx& c;
+            int saved;
+            Reserve(Ctx& c_) : c(c_), saved(c_.tc_sm_reserve) {
+              const int r = c.opts.eig_reserved_sms;
+              c.tc_sm_reserve = r == 0 ? 32 : std::max(0, r);
+            }
+            ~Reserve() { c.tc_sm_reserve = saved; }
+          } reserve(c);
           for (size_t fi = 0; fi < fams.size(); ++fi) build_fused_ahead(c, *fams[fi], next, right, ah[fi]);
         };
       disc = truncate(c, *target, l, xb.d(), M1, right, nextf);

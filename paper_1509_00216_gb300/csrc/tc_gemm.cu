@@ -1,17 +1,20 @@
 // Tensor-core sigma path for sm_103a: a grouped GEMM whose operand tiles are
 // staged by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a shared-memory
-// ring (4 stages of one A and one B tile; 2 stages in split mode, where a
-// stage holds the hi and lo tiles of both operands) and multiplied by
+// ring (as many stages of one A and one B tile as the launch's N-tile cap
+// leaves room for: 4 to 8, or 2 to 4 in split mode, where a stage holds the
+// hi and lo tiles of both operands) and multiplied by
 // tcgen05.mma (kind::f16 with BF16 operands, or kind::tf32) into an FP32
 // accumulator in tensor memory.  One thread issues TMA, one thread issues
-// MMA, and four epilogue warps drain a double-buffered accumulator with
+// MMA, and eight epilogue warps drain a double-buffered accumulator with
 // tcgen05.ld.
 //
 // Each task carries its own tensor maps, so the uneven quantum-number
 // sectors of one sigma product (every operator class, every middle sector)
-// run in one launch per phase.  The epilogue either stores rows with a
-// batched row remap (phase 1 writes the stacked T_w^T blocks) or adds FP32
-// partial sums atomically (phase 2, split over the channel dimension K).
+// run in one launch per phase, and a task may read its K range as a list of
+// runs (the non-zero local pieces of the fused operators).  The epilogue
+// either stores rows with a batched row remap (phase 1 writes the stacked
+// T_w^T blocks) or stores the FP32 partial sum of its K split at the split's
+// own offset (phase 2; a fixed-order reduction adds the splits).
 // Every mbarrier wait is bounded (a launch argument); on expiry the kernel
 // records an error flag and stops issuing work, then waits (with a separate,
 // fixed bound) for the TMA loads and tensor-core products it already issued,
@@ -19,6 +22,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <array>
 #include <atomic>
 #include <cstring>
 #include <map>
@@ -59,6 +63,14 @@ struct alignas(64) TcTask {
                         // pair a sentinel holding the task's step count), then
                         // per K split the run its first step lies in
   int nkr;
+  // column pieces (npc > 0, modes 1, 2, 3, 5): output column c of row m
+  // (channel w = m / rpb, row r = m % rpb) lies in the piece p with
+  // pcs[p] <= c < pcs[p + 1] and goes to C[r ldc + pcb[p] + w pcw[p] + c - pcs[p]];
+  // piece starts, bases and strides are multiples of 8
+  int npc;
+  int pcs[5];
+  int pcw[4];
+  long long pcb[4];
 };
 
 namespace {
@@ -81,7 +93,8 @@ __host__ __device__ __forceinline__ int ring_stages(int cap, bool split) {
 }
 constexpr int ACC_COLS = 256;                // one FP32 accumulator (N <= 256)
 constexpr int TMEM_COLS = 2 * ACC_COLS;      // double-buffered
-constexpr int TC_THREADS = 192;              // TMA warp, MMA warp, 4 epilogue warps
+constexpr int EPI_WARPS = 8;                 // two per tensor-memory lane quarter, splitting the columns
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // TMA warp, MMA warp, epilogue warps
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // default bound on every mbarrier wait (2 s)
 constexpr unsigned long long DRAIN_NS = 2000000000ull;  // bound on the drain of issued work after an abort
 
@@ -410,12 +423,67 @@ __device__ __forceinline__ void store_row(const TcTask* T, long long roff, int c
   }
 }
 
+// Writes 8 accumulator values (v[0..7], FP32 bits) at element offset `off`
+// (a multiple of 8) in the task's output mode, as 16-byte vectors.
+__device__ __forceinline__ void store8(const TcTask* T, long long off, const uint32_t* v) {
+  if (T->mode == 2) {
+    float4* d = reinterpret_cast<float4*>((float*)T->C + off);
+    d[0] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]), __uint_as_float(v[3]));
+    d[1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]), __uint_as_float(v[6]), __uint_as_float(v[7]));
+    return;
+  }
+  uint32_t ph[4], pm[4], pl[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+    const float2 hf = __bfloat1622float2(h);
+    const float r0 = f0 - hf.x, r1 = f1 - hf.y;
+    const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+    const float2 mf = __bfloat1622float2(m);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+    ph[j] = *reinterpret_cast<const uint32_t*>(&h);
+    pm[j] = *reinterpret_cast<const uint32_t*>(&m);
+    pl[j] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+  __nv_bfloat16* C = (__nv_bfloat16*)T->C + off;
+  const uint4 h4 = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+  *reinterpret_cast<uint4*>(C) = h4;
+  if (T->mode == 3) {
+    // two-term split: lo = f - hi, which is the BF16 rounding of the middle piece
+    *reinterpret_cast<uint4*>(C + T->soff) = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+  } else if (T->mode == 5) {
+    // three-piece split as the six B-side blocks [h m m h l h]
+    const uint4 m4 = make_uint4(pm[0], pm[1], pm[2], pm[3]);
+    *reinterpret_cast<uint4*>(C + T->soff) = m4;
+    *reinterpret_cast<uint4*>(C + 2 * T->soff) = m4;
+    *reinterpret_cast<uint4*>(C + 3 * T->soff) = h4;
+    *reinterpret_cast<uint4*>(C + 4 * T->soff) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    *reinterpret_cast<uint4*>(C + 5 * T->soff) = h4;
+  }
+}
+
+// One accumulator row segment (columns c0 .. c0 + nv - 1, c0 a multiple of
+// 32, nv a multiple of 8) of a task with column pieces: every group of 8
+// columns lies in one piece.
+__device__ __forceinline__ void store_row_pieces(const TcTask* T, long long rbase, int w, int c0, int nv,
+                                                 const uint32_t* v) {
+#pragma unroll
+  for (int g = 0; g < 4; ++g) {
+    if (8 * g >= nv) break;
+    const int c = c0 + 8 * g;
+    int p = 0;
+    while (p + 1 < T->npc && c >= T->pcs[p + 1]) ++p;
+    store8(T, rbase + T->pcb[p] + (long long)w * T->pcw[p] + (c - T->pcs[p]), v + 8 * g);
+  }
+}
+
 template <int PREC, bool SPLIT>
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
                                                                  long long total, int* err,
                                                                  unsigned long long wait_ns, int cap) {
   // Warp roles: warp 0 issues TMA, warp 1 issues MMA (and owns the tensor
-  // memory), warps 2..5 drain a double-buffered accumulator, so the loads and
+  // memory), warps 2..9 drain a double-buffered accumulator, so the loads and
   // products of the next tile overlap the epilogue of the previous one.
   extern __shared__ uint8_t smem_raw[];
   // every task of the launch has ntile <= cap; the ring holds as many stages
@@ -441,7 +509,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+      mbar_init(&acc_empty[b], EPI_WARPS);  // one arrival per epilogue warp
     }
     mbar_init(drain, 1);
     *s_abort = 0;
@@ -567,8 +635,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
       mbar_wait(drain, 0u, err, 6, DRAIN_NS);
     }
   } else {
-    // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31
+    // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31 (the
+    // lanes its position in the warpgroup may access), the two warps of one
+    // quarter taking alternate 32-column chunks
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     uint32_t tcount = 0;
     int ti = 0;
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
@@ -584,18 +655,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
       const int row = row0 + quarter * 32 + lane;
       const uint32_t taddr = tmem + buf * ACC_COLS + ((uint32_t)(quarter * 32) << 16);
       const bool live = row < T->m;
+      const bool pieces = T->npc > 0;
       long long roff = 0;
       if (live)
-        roff = (long long)tc.b * T->cbatch + (long long)tc.ks * T->kstride + (long long)(row / T->rpb) * T->bstride +
-               (long long)(row % T->rpb) * T->ldc;
-      for (int cb = 0; cb < ntile; cb += 32) {
+        roff = pieces ? (long long)(row % T->rpb) * T->ldc
+                      : (long long)tc.b * T->cbatch + (long long)tc.ks * T->kstride +
+                            (long long)(row / T->rpb) * T->bstride + (long long)(row % T->rpb) * T->ldc;
+      const int wch = live ? row / T->rpb : 0;
+      for (int cb = 32 * half; cb < ntile; cb += 64) {
         uint32_t v[32];
         tmem_ld32(taddr + cb, v);
         if (!live) continue;
         const int c0 = col0 + cb;
         const int nv = min(32, T->n - c0);
         if (nv <= 0) continue;
-        store_row(T, roff, c0, nv, v);
+        if (pieces) store_row_pieces(T, roff, wch, c0, nv, v);
+        else store_row(T, roff, c0, nv, v);
       }
       fence_before();
       __syncwarp();
@@ -882,7 +957,8 @@ unsigned long long wait_bound_ns(const Ctx& c) {
 
 void launch_tc(Ctx& c, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err, int cap = 256) {
   if (total <= 0 || ntasks <= 0) return;
-  int grid = (int)std::min<long long>(total, (long long)sm_count(c));
+  const int sms = std::max(1, sm_count(c) - std::max(0, c.tc_sm_reserve));
+  int grid = (int)std::min<long long>(total, (long long)sms);
   launch_tc_stream(c.s(), grid, prec, d_tasks, ntasks, total, err, wait_bound_ns(c), cap);
   cuda_check(cudaGetLastError(), "tc_gemm launch");
   c.st.kernel_launches++;
@@ -931,6 +1007,14 @@ void check_err(Ctx& c, DBuf& err) {
 
 }  // namespace
 
+// Rows of the input vector's low-precision copy before local state s of
+// fused sector f, every local-state piece rounded up to 8 rows (s = 4: all).
+long rows8(const Fused& F, int f, int s) {
+  long r = 0;
+  for (int t = 0; t < s && t < 4; ++t) r += pad8(piece_dim(F, f, t));
+  return r;
+}
+
 // Low-precision state of one sigma plan.
 struct TcState {
   int layout = -1;      // operand precision class: TF32, BF16 or BF16X3 (the
@@ -938,7 +1022,13 @@ struct TcState {
   DBuf lcat, rstk, tt, x, conv, convx, err;
   std::vector<long> lcat_off, K8, tt_off, x_off;
   std::vector<long> stk_off;
-  std::vector<std::vector<long>> koff8;   // per bra key: channel-block offsets in the padded K
+  // K layout per bra key: the operator classes (segments) side by side, and
+  // inside a segment one block per ket local state s holding that piece of
+  // every channel (channel stride pad8(d_s)), so that the pieces a row block
+  // reaches in the pass-through channels form one contiguous K run.
+  // kblk[bi][g][s] = start of block s of segment g (-1: the ket sector has
+  // no piece of state s).
+  std::vector<std::vector<std::array<long, 4>>> kblk;
   std::vector<ConvTask> xconv;
   // Phase-1 units: the rows of one R' stack with bra local state so (piece
   // of dimension d at row boff of the bra sector) for channels w0 .. w1-1
@@ -1006,17 +1096,24 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   S->mL = fused_piece_masks(W, lf.p, true);
   S->cstartL = W.bond[lf.p + 1].class_start;
   const std::vector<uint16_t> mR = rf.ext ? std::vector<uint16_t>() : fused_piece_masks(W, rf.p, false);
-  // padded K layout per bra key: each channel block width rounded up to 8
+  // piece-major K layout per bra key, every piece rounded up to 8 columns
   S->K8.assign(nbk, 0);
   S->lcat_off.assign(nbk, 0);
   S->tt_off.assign(nbk, 0);
-  std::vector<std::vector<long>> koff8(nbk);
+  S->kblk.assign(nbk, {});
   long lsz = 0, tsz = 0;
   for (size_t bi = 0; bi < nbk; ++bi) {
     long K8 = 0;
     for (const auto& sg : lf.seg[bi]) {
-      koff8[bi].push_back(K8);
-      K8 += (long)sg.nw * pad8(sg.width);
+      const int fk = lf.kk[sg.kidx];
+      std::array<long, 4> b{-1, -1, -1, -1};
+      for (int sn = 0; sn < 4; ++sn) {
+        const int d = piece_dim(lf.FLk, fk, sn);
+        if (d == 0) continue;
+        b[sn] = K8;
+        K8 += (long)sg.nw * pad8(d);
+      }
+      S->kblk[bi].push_back(b);
     }
     S->K8[bi] = K8;
     S->lcat_off[bi] = lsz;
@@ -1057,11 +1154,14 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
       if (d > 0) S->u2.push_back({(int)bi, so, d, piece_off(lf.FLb, fb, so)});
     }
   }
+  // the input vector's copy keeps its rows (the fused left index) with every
+  // local-state piece rounded up to 8 rows, so that phase 1's output columns
+  // come in groups of 8 inside one piece
   S->x_off.assign(nkk, 0);
   long xsz = 0;
   for (size_t ki = 0; ki < nkk; ++ki) {
     S->x_off[ki] = xsz;
-    xsz += pad8((long)lf.FLk.d[lf.kk[ki]] * sp * pad8(rf.FRk.d[rf.kk[ki]]));
+    xsz += pad8(rows8(lf.FLk, lf.kk[ki], 4) * sp * pad8(rf.FRk.d[rf.kk[ki]]));
   }
   auto zalloc = [&](DBuf& b, long elems, int e) {
     b.alloc(&c, std::max<long>(elems * e, 16));
@@ -1109,8 +1209,8 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
           if (dr == 0 || dc == 0) continue;
           const long ro = piece_off(lf.FLb, fb, so), co = piece_off(lf.FLk, fk, sn);
           conv(lf.data.d() + lf.off[bi] + ro * K + sg.koff + (long)w * sg.width + co, (int)K,
-               (char*)S->lcat.p + (size_t)(S->lcat_off[bi] + ro * pitch + koff8[bi][g] + (long)w * pad8(sg.width) + co) * es,
-               (int)pitch, dr, dc, w1 - w, sg.width, pad8(sg.width), S->K8[bi]);
+               (char*)S->lcat.p + (size_t)(S->lcat_off[bi] + ro * pitch + S->kblk[bi][g][sn] + (long)w * pad8(dc)) * es,
+               (int)pitch, dr, dc, w1 - w, sg.width, pad8(dc), S->K8[bi]);
         }
         w = w1;
       }
@@ -1135,20 +1235,24 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   // per-call conversion of the input vector (B side of phase 1)
   S->xconv.clear();
   for (size_t ki = 0; ki < nkk; ++ki) {
-    ConvTask t;
-    std::memset(&t, 0, sizeof(t));
-    t.src = P.xin.d() + P.off_k[ki];
-    t.dst = (char*)S->x.p + (size_t)S->x_off[ki] * es;
-    t.rows = lf.FLk.d[lf.kk[ki]];
-    t.cols = rf.FRk.d[rf.kk[ki]];
-    t.src_ld = t.cols;
-    t.dst_ld = (int)(sp * pad8(t.cols));
-    t.batch = 1;
-    t.pattern = six ? 3 : 0;
-    t.soff = pad8(t.cols);
-    S->xconv.push_back(t);
+    const int fl = lf.kk[ki], rk = rf.FRk.d[rf.kk[ki]];
+    for (int s1 = 0; s1 < 4; ++s1) {
+      const int d1 = piece_dim(lf.FLk, fl, s1);
+      if (d1 == 0) continue;
+      ConvTask t;
+      std::memset(&t, 0, sizeof(t));
+      t.src = P.xin.d() + P.off_k[ki] + (long)piece_off(lf.FLk, fl, s1) * rk;
+      t.dst = (char*)S->x.p + (size_t)(S->x_off[ki] + rows8(lf.FLk, fl, s1) * sp * pad8(rk)) * es;
+      t.rows = d1;
+      t.cols = rk;
+      t.src_ld = rk;
+      t.dst_ld = (int)(sp * pad8(rk));
+      t.batch = 1;
+      t.pattern = six ? 3 : 0;
+      t.soff = pad8(rk);
+      S->xconv.push_back(t);
+    }
   }
-  S->koff8 = koff8;
   // algorithmic bytes of each variant, per BF16 (or TF32) piece read or
   // written: the non-zero pieces of the fused operators and the parts of the
   // vector and of T they multiply, each read once; T and sigma written once
@@ -1284,7 +1388,7 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
     const int bi = st.bidx, ki = st.kidx;
     const LeftFused::Seg* sg = lf.find_seg(bi, st.cls);
     const size_t g = sg - lf.seg[bi].data();
-    const int fk = rf.kk[ki], rk = rf.FRk.d[fk], lk = lf.FLk.d[lf.kk[ki]];
+    const int fk = rf.kk[ki], rk = rf.FRk.d[fk];
     const long pitch = sp * pad8(rk);
     const int kk = v == 1 ? (int)pitch : rk;
     std::vector<std::pair<long, long>> rg;
@@ -1297,16 +1401,36 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
     std::vector<KRun> runs = merge_runs(rg, KT);
     const int steps = (int)total_steps(runs);
     if (steps == 0) continue;   // the ket sector has none of the unit's pieces: T stays zero there
-    r1.push_back(std::move(runs));
     const long ldc = sp * S->K8[bi];
-    void* C = (char*)S->tt.p +
-              (size_t)(S->tt_off[bi] + S->koff8[bi][g] + (long)u.w0 * pad8(lk) + (long)u.boff * ldc) * es;
     // split tasks: lo parts in block 2 of both operands (and of the output)
     const long long so = v == 1 ? S->K8[bi] : 2 * S->K8[bi];
-    t1.push_back(make_task(c, kp, (char*)S->rstk.p + (size_t)(S->stk_off[u.si] + u.row0 * pitch) * es, pitch,
-                           (char*)S->x.p + (size_t)S->x_off[ki] * es, pitch, (u.w1 - u.w0) * u.d, lk, kk, C, (int)ldc,
-                           u.d, pad8(lk), mode1, 1, six ? so : 0, six ? 2 * pad8(rk) : 0, 1, 0, 0, 0, 0, cap,
-                           steps));
+    // the output columns (psi's padded rows) are scattered by local-state
+    // piece s1 to block s1 of the segment (piece-major K layout), channel w
+    // of the unit at stride pad8(d1)
+    const int fl = lf.kk[ki];
+    const long n8 = rows8(lf.FLk, fl, 4);
+    void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + (long)u.boff * ldc) * es;
+    TcTask t = make_task(c, kp, (char*)S->rstk.p + (size_t)(S->stk_off[u.si] + u.row0 * pitch) * es, pitch,
+                         (char*)S->x.p + (size_t)S->x_off[ki] * es, pitch, (u.w1 - u.w0) * u.d, (int)n8, kk, C,
+                         (int)ldc, u.d, 0, mode1, 1, six ? so : 0, six ? 2 * pad8(rk) : 0, 1, 0, 0, 0, 0, cap, steps);
+    long long last = 0;
+    for (int s1 = 0; s1 < 4; ++s1) {
+      const int d1 = piece_dim(lf.FLk, fl, s1);
+      if (d1 == 0) continue;
+      MPSLCC_REQUIRE(S->kblk[bi][g][s1] >= 0 && t.npc < 4, ST_INTERNAL, "phase-1 column pieces");
+      t.pcs[t.npc] = (int)rows8(lf.FLk, fl, s1);
+      t.pcw[t.npc] = (int)pad8(d1);
+      t.pcb[t.npc] = S->kblk[bi][g][s1] + (long long)u.w0 * pad8(d1);
+      last = std::max(last, (long long)(u.d - 1) * ldc + t.pcb[t.npc] + (long long)(u.w1 - u.w0) * pad8(d1) - 1);
+      t.npc++;
+    }
+    t.pcs[t.npc] = (int)n8;
+    if (t.npc == 0) continue;
+    if (mode1 == 3) last += so;
+    if (mode1 == 5) last += 5 * so;
+    c.check_bytes(C, (last + 1) * (mode1 == 2 ? 4 : 2), "phase-1 piece output");
+    r1.push_back(std::move(runs));
+    t1.push_back(t);
   }
   // phase 2: sigma = Lcat Tt^T per unit (rows of one bra local state of a
   // middle sector), over the K runs of the channel pieces those rows reach,
@@ -1323,12 +1447,13 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
       for (size_t g = 0; g < lf.seg[bi].size(); ++g) {
         const auto& sg = lf.seg[bi][g];
         const int fk = lf.kk[sg.kidx], c0 = S->cstartL[sg.cls];
-        for (int w = 0; w < sg.nw; ++w) {
-          const int row = (S->mL[c0 + w] >> (4 * u.so)) & 15;
-          for (int sn = 0; sn < 4; ++sn) {
-            if (!(row >> sn & 1)) continue;
-            const long co = (long)j * S->K8[bi] + S->koff8[bi][g] + (long)w * pad8(sg.width) + piece_off(lf.FLk, fk, sn);
-            rg.push_back({co, co + piece_dim(lf.FLk, fk, sn)});
+        for (int sn = 0; sn < 4; ++sn) {
+          if (S->kblk[bi][g][sn] < 0) continue;
+          const int d = piece_dim(lf.FLk, fk, sn);
+          for (int w = 0; w < sg.nw; ++w) {
+            if (!((S->mL[c0 + w] >> (4 * u.so + sn)) & 1)) continue;
+            const long co = (long)j * S->K8[bi] + S->kblk[bi][g][sn] + (long)w * pad8(d);
+            rg.push_back({co, co + d});
           }
         }
       }
@@ -1700,6 +1825,7 @@ void tc_gemm_noalloc(int device, cudaStream_t stream, int prec, int m, int n, in
 // [batch][rows][6 K] stacks read through 3D tensor maps.
 void run_gemms_tc(Ctx& c, std::vector<GemmTask>& tasks) {
   if (tasks.empty()) return;
+  for (const auto& t : tasks) MPSLCC_REQUIRE(!t.kr, ST_INTERNAL, "K-run task on the FP64 emulation path");
   const double th0 = c.opts.verbose >= 2 ? wall_seconds() : 0.0;
   struct Key {
     const double* p;
