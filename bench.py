@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the mixed-vs-FP64 comparison on a window of middle positions")
     ap.add_argument("--compare-window", type=int, default=4)
+    ap.add_argument("--residual-fp64", action="store_true",
+                    help="mixed sweeps with FP64 right-hand sides, residuals and environments")
     ap.add_argument("--eig-reserved-sms", type=int, default=0,
                     help="SMs left to the truncation's eigensolvers while fused operators are built (0: library default)")
     ap.add_argument("--verbose", type=int, default=0,
@@ -362,7 +364,7 @@ def gpu_arm(args, rank, world, local_rank):
     M1 = args.M1 or c["M1"]
     prec = PREC[args.prec]
     ctx = mp.Context(device=local_rank, prec=prec, tol=1e-8, max_iter=60, torch_memory=True, verbose=args.verbose,
-                     eig_reserved_sms=args.eig_reserved_sms,
+                     eig_reserved_sms=args.eig_reserved_sms, residual_fp64=args.residual_fp64,
                      init_guess=1 if args.dmrg_init == "product" else 0)
     ctx.build_mpo(c["h"], c["V"], c["n_alpha"] + c["n_beta"], 0)
     ctx.set_spaces(c["n_core"], c["n_active"])
@@ -400,7 +402,7 @@ def gpu_arm(args, rank, world, local_rank):
                           "tc_phase1_s": st["tc_phase1_seconds"], "tc_phase2_s": st["tc_phase2_seconds"],
                           "tc_phase1_bytes": st["tc_phase1_bytes"], "tc_phase2_bytes": st["tc_phase2_bytes"],
                           "sigma_flops": st["sigma_flops"], "calls": st["sigma_calls"],
-                          "tile_caps": {k: st["tc_launches_" + k] for k in ("n256", "n128", "n64")}}), flush=True)
+                          "tile_caps": {k: st["tc_launches_" + k] for k in ("n256", "n128", "n64", "n64x2")}}), flush=True)
         ctx.close()
         return
     ctx.reset_stats()
@@ -487,6 +489,7 @@ def gpu_arm(args, rank, world, local_rank):
                 ms_per_step=dev_s / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype={0: "f64", 1: "tf32", 2: "bf16", 3: "bf16x3"}[prec], data="synthetic",
                 config=workload_config(c, M0, M1, world),
+                residual_prec="f64" if (prec == 0 or args.residual_fp64) else "bf16x6",
                 sweep_s=dev_s / args.steps, sigma_calls=sweep_calls, sigma_kernel_s=kern,
                 stage_s={k: st[k] for k in ("t_plan", "t_rhs", "t_solve", "t_trunc", "t_env", "t_fuse_left", "t_fuse_right", "t_tc_prepare")},
                 fused_ahead={"used": st["ahead_used"], "missed": st["ahead_missed"]},

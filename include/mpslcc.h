@@ -119,6 +119,12 @@ typedef struct {
                             eigensolvers run on their side streams (the
                             next position's fused operators are built
                             meanwhile): 0 = default (32), < 0 = none       */
+  int residual_fp64;     /* mixed-precision LCC sweeps: 1 forms the
+                            right-hand side and the refinement residuals
+                            with FP64 products on FP64 environments and
+                            fused operators (the inner solves stay on the
+                            tensor cores); 0 (default): BF16X6 products on
+                            tensor-core environments                        */
 } mpslcc_opts;
 
 typedef struct {
@@ -195,6 +201,8 @@ typedef struct {
                                  at most 256 rows (chosen by the autotuner)  */
   long long tc_launches_n128;
   long long tc_launches_n64;
+  long long tc_launches_n64x2; /* ... N tiles of at most 64 rows, two CTAs
+                                  per SM                                    */
 } mpslcc_stats;
 
 /* Fill *opts with defaults (device 0, FP64, tol 1e-10, max_iter 200, auto

@@ -46,7 +46,8 @@ class Opts(C.Structure):
                 ("refine_steps", C.c_int), ("seed", C.c_ulonglong), ("verbose", C.c_int),
                 ("alloc", _ALLOC), ("free", _FREE), ("alloc_user", C.c_void_p),
                 ("init_guess", C.c_int), ("wait_timeout_s", C.c_double), ("tc_environments", C.c_int),
-                ("autotune", C.c_int), ("eig_reserved_sms", C.c_int)]
+                ("autotune", C.c_int), ("eig_reserved_sms", C.c_int),
+                ("residual_fp64", C.c_int)]
 
 
 class Energies(C.Structure):
@@ -71,7 +72,7 @@ class Stats(C.Structure):
                 ("ahead_used", C.c_longlong), ("ahead_missed", C.c_longlong), ("n_noconv", C.c_longlong),
                 ("n_indefinite", C.c_longlong), ("n_j_rise", C.c_longlong), ("max_rel_residual", C.c_double),
                 ("tune_trials", C.c_longlong), ("tc_launches_n256", C.c_longlong), ("tc_launches_n128", C.c_longlong),
-                ("tc_launches_n64", C.c_longlong)]
+                ("tc_launches_n64", C.c_longlong), ("tc_launches_n64x2", C.c_longlong)]
 
 
 def _load():
@@ -162,7 +163,8 @@ class Context:
 
     def __init__(self, device=0, prec=FP64, tol=1e-10, max_iter=200, seed=7, verbose=0, refine_steps=4,
                  davidson_max_subspace=24, torch_memory=False, init_guess=0, wait_timeout_s=0.0, alloc=None,
-                 stream=None, tc_environments=False, autotune=True, eig_reserved_sms=0):
+                 stream=None, tc_environments=False, autotune=True, eig_reserved_sms=0,
+                 residual_fp64=False):
         L = lib()
         o = Opts()
         L.mpslcc_default_opts(C.byref(o))
@@ -179,15 +181,32 @@ class Context:
         o.tc_environments = 1 if tc_environments else 0
         o.autotune = 1 if autotune else 0
         o.eig_reserved_sms = int(eig_reserved_sms)
+        o.residual_fp64 = 1 if residual_fp64 else 0
         if stream is not None:
             o.stream = C.c_void_p(stream)
         self._cb = None
         self.last_status = 0
+        # The allocator callbacks never let an exception escape: ctypes would
+        # print it and hand the library an unset return value (not NULL), a
+        # pointer the kernels would then use.  A failed allocation returns
+        # NULL, which the library turns into MPSLCC_E_NOMEM.
         if alloc is not None:
             # caller-provided (alloc(nbytes) -> int pointer or 0, free(ptr, nbytes)) pair
             a_fn, f_fn = alloc
-            self._cb = (_ALLOC(lambda nbytes, user: a_fn(int(nbytes)) or None),
-                        _FREE(lambda ptr, nbytes, user: f_fn(ptr, int(nbytes))))
+
+            def _a(nbytes, user):
+                try:
+                    return a_fn(int(nbytes)) or None
+                except Exception:
+                    return None
+
+            def _f(ptr, nbytes, user):
+                try:
+                    f_fn(ptr, int(nbytes))
+                except Exception:
+                    pass
+
+            self._cb = (_ALLOC(_a), _FREE(_f))
             o.alloc, o.free = self._cb
         elif torch_memory and device >= 0:
             import torch
@@ -195,10 +214,16 @@ class Context:
             o.stream = C.c_void_p(stream.cuda_stream)
 
             def _a(nbytes, user):
-                return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), device, stream)
+                except Exception:   # torch.OutOfMemoryError among others
+                    return None
 
             def _f(ptr, nbytes, user):
-                torch.cuda.caching_allocator_delete(int(ptr))
+                try:
+                    torch.cuda.caching_allocator_delete(int(ptr))
+                except Exception:
+                    pass
 
             self._cb = (_ALLOC(_a), _FREE(_f))
             o.alloc, o.free = self._cb

@@ -671,6 +671,7 @@ mpslcc_status mpslcc_get_stats(mpslcc_ctx* ctx, mpslcc_stats* out) {
     out->tc_launches_n256 = c.st.tc_cap_launches[0];
     out->tc_launches_n128 = c.st.tc_cap_launches[1];
     out->tc_launches_n64 = c.st.tc_cap_launches[2];
+    out->tc_launches_n64x2 = c.st.tc_cap_launches[3];
   });
 }
 

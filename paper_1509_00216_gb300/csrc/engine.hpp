@@ -214,7 +214,7 @@ struct Stats {
   long long n_noconv = 0, n_indefinite = 0, n_j_rise = 0;
   double max_rel_residual = 0;
   long long tune_trials = 0;
-  long long tc_cap_launches[3] = {0, 0, 0};   // sigma launches per N-tile cap 256 / 128 / 64
+  long long tc_cap_launches[4] = {0, 0, 0, 0};   // sigma launches per tile shape: cap 256 / 128 / 64, 64 on 2 CTAs/SM
 };
 
 // Solver outcome counters of the current sweep call (reset per call).
@@ -335,7 +335,7 @@ struct Ctx {
   };
   struct TuneEntry {
     double bytes = 0;
-    double ms[3] = {0, 0, 0};
+    double ms[4] = {0, 0, 0, 0};
     int tried = 0, best = -1;
   };
   std::map<TuneKey, TuneEntry> tune;

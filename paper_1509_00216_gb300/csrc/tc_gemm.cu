@@ -66,7 +66,7 @@ struct alignas(64) TcTask {
   // column pieces (npc > 0, modes 1, 2, 3, 5): output column c of row m
   // (channel w = m / rpb, row r = m % rpb) lies in the piece p with
   // pcs[p] <= c < pcs[p + 1] and goes to C[r ldc + pcb[p] + w pcw[p] + c - pcs[p]];
-  // piece starts, bases and strides are multiples of 8
+  // piece starts, bases and strides are multiples of 8 (of 16 for sigma)
   int npc;
   int pcs[5];
   int pcw[4];
@@ -77,24 +77,36 @@ namespace {
 
 constexpr int MAX_DEVICES = 128;
 constexpr int A_BYTES = 128 * 128;           // 128 rows x 128 bytes
-constexpr int RING_BYTES = 192 * 1024;       // operand stages; a launch's N-tile cap sets their size
 constexpr int MAX_STAGES = 8;
-constexpr int SMEM_BYTES = RING_BYTES + 1024 + 256;
+constexpr int STG_ROW = 80;                  // epilogue staging: bytes per row (64 used)
+constexpr int STG_WARP = 32 * STG_ROW;       // per epilogue warp
 
-// Stages of the shared-memory ring for a launch whose tasks use N tiles of at
+// Kernel configurations.  CFG 0, one CTA per SM: a 192 KB operand ring,
+// N tiles up to 256 rows, a double-buffered 2 x 256-column accumulator and
+// eight epilogue warps (two per tensor-memory lane quarter).  CFG 1, two CTAs
+// per SM for tasks of short K and small tiles, whose time goes to per-tile
+// latency: a 96 KB ring, N tiles up to 64 rows, 2 x 64 accumulator columns
+// (each CTA allocates 128 of the SM's 512) and four epilogue warps.
+template <int CFG> struct KCfg {
+  static constexpr int RING = CFG == 0 ? 192 * 1024 : 96 * 1024;
+  static constexpr int ACC = CFG == 0 ? 256 : 64;
+  static constexpr int TMEM = 2 * ACC;
+  static constexpr int EPI = CFG == 0 ? 8 : 4;
+  static constexpr int THREADS = 64 + 32 * EPI;   // TMA warp, MMA warp, epilogue warps
+  static constexpr int MINB = CFG == 0 ? 1 : 2;
+  static constexpr int SMEM = RING + 1024 + 256 + EPI * STG_WARP;
+};
+
+// Stages of a ring of `ring` bytes for a launch whose tasks use N tiles of at
 // most `cap` rows (64, 128 or 256): a stage holds one A tile (128 x 128 B) and
 // one B tile (cap x 128 B), twice in split mode (hi and lo parts).
 __host__ __device__ __forceinline__ int stage_bytes(int cap, bool split) {
   return (A_BYTES + cap * 128) * (split ? 2 : 1);
 }
-__host__ __device__ __forceinline__ int ring_stages(int cap, bool split) {
-  const int n = RING_BYTES / stage_bytes(cap, split);
+__host__ __device__ __forceinline__ int ring_stages(int ring, int cap, bool split) {
+  const int n = ring / stage_bytes(cap, split);
   return n < MAX_STAGES ? n : MAX_STAGES;
 }
-constexpr int ACC_COLS = 256;                // one FP32 accumulator (N <= 256)
-constexpr int TMEM_COLS = 2 * ACC_COLS;      // double-buffered
-constexpr int EPI_WARPS = 8;                 // two per tensor-memory lane quarter, splitting the columns
-constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;   // TMA warp, MMA warp, epilogue warps
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // default bound on every mbarrier wait (2 s)
 constexpr unsigned long long DRAIN_NS = 2000000000ull;  // bound on the drain of issued work after an abort
 
@@ -463,6 +475,123 @@ __device__ __forceinline__ void store8(const TcTask* T, long long off, const uin
   }
 }
 
+// Per-tile values of a column-piece task (phase 1 of sigma) kept in registers
+// by the epilogue: in the staged store each lane writes rows q * 8 + lane / 4
+// (q = 0..3) of its warp's 32, at row offset roff[q] of channel wch[q].
+struct PieceTile {
+  __nv_bfloat16* C;
+  long long soff;
+  long long roff[4];
+  int wch[4];
+  bool rlive[4];
+  int n, mode, npc;
+  int pcs1, pcs2, pcs3;
+  int pcw0, pcw1, pcw2, pcw3;
+  long long pb0, pb1, pb2, pb3;   // pcb[p] - pcs[p]
+};
+
+__device__ __forceinline__ void piece_tile(const TcTask* T, int rw0, int lane, PieceTile& P) {
+  P.C = (__nv_bfloat16*)T->C;
+  P.soff = T->soff;
+  P.n = T->n;
+  P.mode = T->mode;
+  P.npc = T->npc;
+  const int m = T->m, rpb = T->rpb;
+  const long long ldc = T->ldc;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int row = rw0 + q * 8 + (lane >> 2);
+    const int w = row / rpb;
+    P.rlive[q] = row < m;
+    P.wch[q] = w;
+    P.roff[q] = (long long)(row - w * rpb) * ldc;
+  }
+  P.pcs1 = T->pcs[1];
+  P.pcs2 = T->pcs[2];
+  P.pcs3 = T->pcs[3];
+  P.pcw0 = T->pcw[0];
+  P.pcw1 = T->pcw[1];
+  P.pcw2 = T->pcw[2];
+  P.pcw3 = T->pcw[3];
+  P.pb0 = T->pcb[0] - T->pcs[0];
+  P.pb1 = T->pcb[1] - T->pcs[1];
+  P.pb2 = T->pcb[2] - T->pcs[2];
+  P.pb3 = T->pcb[3] - T->pcs[3];
+}
+
+// A warp's 32 x 32 accumulator chunk (lane i holding row rw0 + i of the tile,
+// columns c0 .. c0 + 31) of a column-piece task with BF16 output, written
+// through the warp's shared-memory staging rows: each store instruction then
+// covers 8 rows x 64 contiguous bytes (whole 32-byte sectors) instead of 32
+// rows x 16 bytes.  All 32 lanes take part.
+__device__ __forceinline__ void store_chunk_staged(const PieceTile& P, uint8_t* stg, int lane, int c0,
+                                                   const uint32_t* v) {
+  const bool three = P.mode == 5;
+  uint32_t ph[16], pm[16], pl[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    const float f0 = __uint_as_float(v[2 * j]), f1 = __uint_as_float(v[2 * j + 1]);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(f0, f1);
+    const float2 hf = __bfloat1622float2(h);
+    const float r0 = f0 - hf.x, r1 = f1 - hf.y;
+    const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+    ph[j] = *reinterpret_cast<const uint32_t*>(&h);
+    pm[j] = *reinterpret_cast<const uint32_t*>(&m);
+    pl[j] = 0u;
+    if (three) {
+      const float2 mf = __bfloat1622float2(m);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(r0 - mf.x, r1 - mf.y);
+      pl[j] = *reinterpret_cast<const uint32_t*>(&l);
+    }
+  }
+  // this lane's 8-column group: its piece's base and channel stride
+  const int col = c0 + 8 * (lane & 3);
+  const bool cl = col < P.n;
+  long long base;
+  int stride;
+  if (P.npc > 3 && col >= P.pcs3) { base = P.pb3; stride = P.pcw3; }
+  else if (P.npc > 2 && col >= P.pcs2) { base = P.pb2; stride = P.pcw2; }
+  else if (P.npc > 1 && col >= P.pcs1) { base = P.pb1; stride = P.pcw1; }
+  else { base = P.pb0; stride = P.pcw0; }
+  base += col;
+  const int nparts = three ? 3 : (P.mode == 3 ? 2 : 1);
+  const long long so = P.soff;
+#pragma unroll
+  for (int part = 0; part < 3; ++part) {
+    if (part >= nparts) break;
+    const uint32_t* src = part == 0 ? ph : (part == 1 ? pm : pl);
+    uint4* mine = reinterpret_cast<uint4*>(stg + lane * STG_ROW);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) mine[q] = make_uint4(src[4 * q], src[4 * q + 1], src[4 * q + 2], src[4 * q + 3]);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int rr = q * 8 + (lane >> 2), g = lane & 3;
+      const uint4 val = *reinterpret_cast<const uint4*>(stg + rr * STG_ROW + g * 16);
+      if (P.rlive[q] && cl) {
+        __nv_bfloat16* C = P.C + P.roff[q] + base + (long long)P.wch[q] * stride;
+        if (three) {
+          // three-piece split as the six B-side blocks [h m m h l h]
+          if (part == 0) {
+            *reinterpret_cast<uint4*>(C) = val;
+            *reinterpret_cast<uint4*>(C + 3 * so) = val;
+            *reinterpret_cast<uint4*>(C + 5 * so) = val;
+          } else if (part == 1) {
+            *reinterpret_cast<uint4*>(C + so) = val;
+            *reinterpret_cast<uint4*>(C + 2 * so) = val;
+          } else {
+            *reinterpret_cast<uint4*>(C + 4 * so) = val;
+          }
+        } else {
+          // hi at +0; in split mode the lo part (the rounded remainder) at +soff
+          *reinterpret_cast<uint4*>(C + (part == 1 ? so : 0)) = val;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // One accumulator row segment (columns c0 .. c0 + nv - 1, c0 a multiple of
 // 32, nv a multiple of 8) of a task with column pieces: every group of 8
 // columns lies in one piece.
@@ -478,8 +607,8 @@ __device__ __forceinline__ void store_row_pieces(const TcTask* T, long long rbas
   }
 }
 
-template <int PREC, bool SPLIT>
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
+template <int PREC, bool SPLIT, int CFG>
+__global__ void __launch_bounds__(KCfg<CFG>::THREADS, KCfg<CFG>::MINB) tc_gemm_kernel(const TcTask* __restrict__ tasks, int ntasks,
                                                                  long long total, int* err,
                                                                  unsigned long long wait_ns, int cap) {
   // Warp roles: warp 0 issues TMA, warp 1 issues MMA (and owns the tensor
@@ -488,7 +617,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
   extern __shared__ uint8_t smem_raw[];
   // every task of the launch has ntile <= cap; the ring holds as many stages
   // of that size as fit (split mode keeps hi and lo tiles of both operands)
-  const int NST = ring_stages(cap, SPLIT);
+  using K = KCfg<CFG>;
+  constexpr int RING_BYTES = K::RING, ACC_COLS = K::ACC, TMEM_COLS = K::TMEM, EPI_WARPS = K::EPI;
+  const int NST = ring_stages(RING_BYTES, cap, SPLIT);
   const int SB = stage_bytes(cap, SPLIT);
   const int BB = cap * 128;                          // B tile bytes in a stage
   constexpr int KT = PREC == MPSLCC_BF16 ? 64 : 32;  // K elements per 128-byte row
@@ -636,10 +767,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
     }
   } else {
     // epilogue: warp w drains tensor-memory lanes 32 (w % 4) .. + 31 (the
-    // lanes its position in the warpgroup may access), the two warps of one
-    // quarter taking alternate 32-column chunks
+    // lanes its position in the warpgroup may access); with eight epilogue
+    // warps the two of one quarter take alternate 32-column chunks
+    constexpr int NHALF = EPI_WARPS / 4;
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
+    uint8_t* stg = smem + RING_BYTES + 256 + (warp - 2) * STG_WARP;
     uint32_t tcount = 0;
     int ti = 0;
     for (long long tile = blockIdx.x; tile < total; tile += gridDim.x, ++tcount) {
@@ -662,9 +795,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const TcTask* __
                       : (long long)tc.b * T->cbatch + (long long)tc.ks * T->kstride +
                             (long long)(row / T->rpb) * T->bstride + (long long)(row % T->rpb) * T->ldc;
       const int wch = live ? row / T->rpb : 0;
-      for (int cb = 32 * half; cb < ntile; cb += 64) {
+      const bool staged = pieces && T->mode != 2;
+      PieceTile PT;
+      if (staged) piece_tile(T, row0 + quarter * 32, lane, PT);
+      for (int cb = 32 * half; cb < ntile; cb += 32 * NHALF) {
         uint32_t v[32];
         tmem_ld32(taddr + cb, v);
+        if (staged) {
+          store_chunk_staged(PT, stg, lane, col0 + cb, v);
+          continue;
+        }
         if (!live) continue;
         const int c0 = col0 + cb;
         const int nv = min(32, T->n - c0);
@@ -778,6 +918,10 @@ inline int esize(int prec) { return prec == MPSLCC_TF32 ? 4 : 2; }
 // kernel operand type: TF32, or BF16 (also for the split BF16x3 mode)
 inline int kprec(int prec) { return prec == MPSLCC_TF32 ? MPSLCC_TF32 : MPSLCC_BF16; }
 inline long pad8(long x) { return (x + 7) / 8 * 8; }
+// local-state pieces of the phase-2 K axis (and of the input vector's rows)
+// start on 16-element boundaries: 32-byte sectors of T are then written whole
+// by one thread, never half by each of two channels
+inline long padp(long x) { return (x + 15) / 16 * 16; }
 
 // 2D K-major operand map: `rows` rows of `cols` logical elements, row pitch
 // `ld` elements; box = box_rows x 128 bytes, 128-byte swizzle.
@@ -926,26 +1070,38 @@ long long plan_tc(std::vector<TcTask>& t) {
 
 // The dynamic shared-memory opt-in is a per-device function attribute: it is
 // set once per (kernel instance, device), the flag kept per device.
-template <int P, bool S>
+template <int P, bool S, int CFG>
 void launch_variant(cudaStream_t st, int grid, const TcTask* d_tasks, int ntasks, long long total, int* err,
                     unsigned long long wait_ns, int cap) {
+  using K = KCfg<CFG>;
   static std::atomic<bool> attr[MAX_DEVICES];
   int dev = 0;
   cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
   MPSLCC_REQUIRE(dev >= 0 && dev < MAX_DEVICES, ST_ARG, "device ordinal out of range");
+  MPSLCC_REQUIRE(cap <= K::ACC, ST_INTERNAL, "N-tile cap above the configuration's accumulator");
   if (!attr[dev].load(std::memory_order_acquire)) {
-    cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<P, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
+    cuda_check(cudaFuncSetAttribute(tc_gemm_kernel<P, S, CFG>, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM),
                "smem attr");
     attr[dev].store(true, std::memory_order_release);
   }
-  tc_gemm_kernel<P, S><<<grid, TC_THREADS, SMEM_BYTES, st>>>(d_tasks, ntasks, total, err, wait_ns, cap);
+  tc_gemm_kernel<P, S, CFG><<<grid, K::THREADS, K::SMEM, st>>>(d_tasks, ntasks, total, err, wait_ns, cap);
 }
 
+template <int CFG>
+void launch_cfg(cudaStream_t st, int grid, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err,
+                unsigned long long wait_ns, int cap) {
+  if (prec == MPSLCC_BF16X3) launch_variant<MPSLCC_BF16, true, CFG>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
+  else if (prec == MPSLCC_BF16)
+    launch_variant<MPSLCC_BF16, false, CFG>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
+  else launch_variant<MPSLCC_TF32, false, CFG>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
+}
+
+// grid = persistent CTAs (at most the configuration's CTAs per SM times the
+// SMs used); cfg 1 needs cap <= 64
 void launch_tc_stream(cudaStream_t st, int grid, int prec, const TcTask* d_tasks, int ntasks, long long total,
-                      int* err, unsigned long long wait_ns = WAIT_NS, int cap = 256) {
-  if (prec == MPSLCC_BF16X3) launch_variant<MPSLCC_BF16, true>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
-  else if (prec == MPSLCC_BF16) launch_variant<MPSLCC_BF16, false>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
-  else launch_variant<MPSLCC_TF32, false>(st, grid, d_tasks, ntasks, total, err, wait_ns, cap);
+                      int* err, unsigned long long wait_ns = WAIT_NS, int cap = 256, int cfg = 0) {
+  if (cfg == 1) launch_cfg<1>(st, grid, prec, d_tasks, ntasks, total, err, wait_ns, cap);
+  else launch_cfg<0>(st, grid, prec, d_tasks, ntasks, total, err, wait_ns, cap);
 }
 
 // bound on each mbarrier wait of a context's tensor-core launches
@@ -955,11 +1111,13 @@ unsigned long long wait_bound_ns(const Ctx& c) {
   return (unsigned long long)(std::min(s, 60.0) * 1e9);
 }
 
-void launch_tc(Ctx& c, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err, int cap = 256) {
+void launch_tc(Ctx& c, int prec, const TcTask* d_tasks, int ntasks, long long total, int* err, int cap = 256,
+               int cfg = 0) {
   if (total <= 0 || ntasks <= 0) return;
   const int sms = std::max(1, sm_count(c) - std::max(0, c.tc_sm_reserve));
-  int grid = (int)std::min<long long>(total, (long long)sms);
-  launch_tc_stream(c.s(), grid, prec, d_tasks, ntasks, total, err, wait_bound_ns(c), cap);
+  const int per_sm = cfg == 1 ? KCfg<1>::MINB : KCfg<0>::MINB;
+  int grid = (int)std::min<long long>(total, (long long)sms * per_sm);
+  launch_tc_stream(c.s(), grid, prec, d_tasks, ntasks, total, err, wait_bound_ns(c), cap, cfg);
   cuda_check(cudaGetLastError(), "tc_gemm launch");
   c.st.kernel_launches++;
   c.st.gemm_launches++;
@@ -1008,10 +1166,10 @@ void check_err(Ctx& c, DBuf& err) {
 }  // namespace
 
 // Rows of the input vector's low-precision copy before local state s of
-// fused sector f, every local-state piece rounded up to 8 rows (s = 4: all).
-long rows8(const Fused& F, int f, int s) {
+// fused sector f, every local-state piece rounded up to 16 rows (s = 4: all).
+long rows_p(const Fused& F, int f, int s) {
   long r = 0;
-  for (int t = 0; t < s && t < 4; ++t) r += pad8(piece_dim(F, f, t));
+  for (int t = 0; t < s && t < 4; ++t) r += padp(piece_dim(F, f, t));
   return r;
 }
 
@@ -1024,8 +1182,9 @@ struct TcState {
   std::vector<long> stk_off;
   // K layout per bra key: the operator classes (segments) side by side, and
   // inside a segment one block per ket local state s holding that piece of
-  // every channel (channel stride pad8(d_s)), so that the pieces a row block
-  // reaches in the pass-through channels form one contiguous K run.
+  // every channel (channel stride padp(d_s): d_s rounded up to 16), so that
+  // the pieces a row block reaches in the pass-through channels form one
+  // contiguous K run.
   // kblk[bi][g][s] = start of block s of segment g (-1: the ket sector has
   // no piece of state s).
   std::vector<std::vector<std::array<long, 4>>> kblk;
@@ -1044,7 +1203,7 @@ struct TcState {
   std::vector<int> cstartL;               // class starts of that bond
   // Task lists per sigma variant v ([0] the layout's own precision: TF32,
   // BF16 or BF16X3; [1] BF16X6, six-block layout only) and N-tile cap
-  // (TC_CAPS), built on first use; phase 2 keeps its K-split FP32 partials
+  // (TC_CAPS[0..2]), built on first use; phase 2 keeps its K-split FP32 partials
   // and the segments of their fixed-order sum.
   struct Lists {
     bool built = false;
@@ -1111,7 +1270,7 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
         const int d = piece_dim(lf.FLk, fk, sn);
         if (d == 0) continue;
         b[sn] = K8;
-        K8 += (long)sg.nw * pad8(d);
+        K8 += (long)sg.nw * padp(d);
       }
       S->kblk[bi].push_back(b);
     }
@@ -1155,13 +1314,13 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
     }
   }
   // the input vector's copy keeps its rows (the fused left index) with every
-  // local-state piece rounded up to 8 rows, so that phase 1's output columns
-  // come in groups of 8 inside one piece
+  // local-state piece rounded up to 16 rows, so that phase 1's output
+  // columns come in groups of 16 inside one piece
   S->x_off.assign(nkk, 0);
   long xsz = 0;
   for (size_t ki = 0; ki < nkk; ++ki) {
     S->x_off[ki] = xsz;
-    xsz += pad8(rows8(lf.FLk, lf.kk[ki], 4) * sp * pad8(rf.FRk.d[rf.kk[ki]]));
+    xsz += pad8(rows_p(lf.FLk, lf.kk[ki], 4) * sp * pad8(rf.FRk.d[rf.kk[ki]]));
   }
   auto zalloc = [&](DBuf& b, long elems, int e) {
     b.alloc(&c, std::max<long>(elems * e, 16));
@@ -1209,8 +1368,8 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
           if (dr == 0 || dc == 0) continue;
           const long ro = piece_off(lf.FLb, fb, so), co = piece_off(lf.FLk, fk, sn);
           conv(lf.data.d() + lf.off[bi] + ro * K + sg.koff + (long)w * sg.width + co, (int)K,
-               (char*)S->lcat.p + (size_t)(S->lcat_off[bi] + ro * pitch + S->kblk[bi][g][sn] + (long)w * pad8(dc)) * es,
-               (int)pitch, dr, dc, w1 - w, sg.width, pad8(dc), S->K8[bi]);
+               (char*)S->lcat.p + (size_t)(S->lcat_off[bi] + ro * pitch + S->kblk[bi][g][sn] + (long)w * padp(dc)) * es,
+               (int)pitch, dr, dc, w1 - w, sg.width, padp(dc), S->K8[bi]);
         }
         w = w1;
       }
@@ -1242,7 +1401,7 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
       ConvTask t;
       std::memset(&t, 0, sizeof(t));
       t.src = P.xin.d() + P.off_k[ki] + (long)piece_off(lf.FLk, fl, s1) * rk;
-      t.dst = (char*)S->x.p + (size_t)(S->x_off[ki] + rows8(lf.FLk, fl, s1) * sp * pad8(rk)) * es;
+      t.dst = (char*)S->x.p + (size_t)(S->x_off[ki] + rows_p(lf.FLk, fl, s1) * sp * pad8(rk)) * es;
       t.rows = d1;
       t.cols = rk;
       t.src_ld = rk;
@@ -1303,7 +1462,12 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
 
 namespace {
 
-constexpr int TC_CAPS[3] = {256, 128, 64};
+// Tile shapes the autotuner chooses from: N-tile cap and kernel configuration
+// (the cap-64 task lists serve both configurations)
+constexpr int NSHAPE = 4;
+constexpr int TC_CAPS[NSHAPE] = {256, 128, 64, 64};
+constexpr int TC_CFG[NSHAPE] = {0, 0, 0, 1};
+inline int list_of(int shape) { return shape < 3 ? shape : 2; }
 
 // K runs of one task: its non-zero columns come as ranges [a, b) of the
 // operands' K extent; each run starts on an 8-element boundary (16-byte TMA
@@ -1406,9 +1570,9 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
     const long long so = v == 1 ? S->K8[bi] : 2 * S->K8[bi];
     // the output columns (psi's padded rows) are scattered by local-state
     // piece s1 to block s1 of the segment (piece-major K layout), channel w
-    // of the unit at stride pad8(d1)
+    // of the unit at stride padp(d1)
     const int fl = lf.kk[ki];
-    const long n8 = rows8(lf.FLk, fl, 4);
+    const long n8 = rows_p(lf.FLk, fl, 4);
     void* C = (char*)S->tt.p + (size_t)(S->tt_off[bi] + (long)u.boff * ldc) * es;
     TcTask t = make_task(c, kp, (char*)S->rstk.p + (size_t)(S->stk_off[u.si] + u.row0 * pitch) * es, pitch,
                          (char*)S->x.p + (size_t)S->x_off[ki] * es, pitch, (u.w1 - u.w0) * u.d, (int)n8, kk, C,
@@ -1418,10 +1582,10 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
       const int d1 = piece_dim(lf.FLk, fl, s1);
       if (d1 == 0) continue;
       MPSLCC_REQUIRE(S->kblk[bi][g][s1] >= 0 && t.npc < 4, ST_INTERNAL, "phase-1 column pieces");
-      t.pcs[t.npc] = (int)rows8(lf.FLk, fl, s1);
-      t.pcw[t.npc] = (int)pad8(d1);
-      t.pcb[t.npc] = S->kblk[bi][g][s1] + (long long)u.w0 * pad8(d1);
-      last = std::max(last, (long long)(u.d - 1) * ldc + t.pcb[t.npc] + (long long)(u.w1 - u.w0) * pad8(d1) - 1);
+      t.pcs[t.npc] = (int)rows_p(lf.FLk, fl, s1);
+      t.pcw[t.npc] = (int)padp(d1);
+      t.pcb[t.npc] = S->kblk[bi][g][s1] + (long long)u.w0 * padp(d1);
+      last = std::max(last, (long long)(u.d - 1) * ldc + t.pcb[t.npc] + (long long)(u.w1 - u.w0) * padp(d1) - 1);
       t.npc++;
     }
     t.pcs[t.npc] = (int)n8;
@@ -1452,7 +1616,7 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
           const int d = piece_dim(lf.FLk, fk, sn);
           for (int w = 0; w < sg.nw; ++w) {
             if (!((S->mL[c0 + w] >> (4 * u.so + sn)) & 1)) continue;
-            const long co = (long)j * S->K8[bi] + S->kblk[bi][g][sn] + (long)w * pad8(d);
+            const long co = (long)j * S->K8[bi] + S->kblk[bi][g][sn] + (long)w * padp(d);
             rg.push_back({co, co + d});
           }
         }
@@ -1548,12 +1712,13 @@ void build_lists(Ctx& c, SigmaPlan& P, TcState* S, int v, int ci) {
 }
 
 // Tile-shape autotuner of the sigma phases.  For every (operator family,
-// position, phase, precision) the first products run once with each N-tile cap
-// (TC_CAPS: 256, 128 and 64 rows, i.e. 4 / 6 / 8 ring stages of BF16 tiles, or
-// 2 / 3 / 4 of split tiles); the cap with the shortest device time is kept
-// for later products of that position, in this and later sweeps, and tuned
-// again when the phase's algorithmic bytes change by more than a fifth.
-// Every cap computes the same numbers (the K splits do not depend on it).
+// position, phase, precision) the first products run once with each shape:
+// N-tile caps of 256, 128 and 64 rows on one CTA per SM (4 / 6 / 8 ring
+// stages of BF16 tiles, or 2 / 3 / 4 of split tiles), and a cap of 64 on two
+// CTAs per SM (configuration 1); the shape with the shortest device time is
+// kept for later products of that position, in this and later sweeps, and
+// tuned again when the phase's algorithmic bytes change by more than a fifth.
+// Every shape computes the same numbers (the K splits do not depend on it).
 Ctx::TuneEntry& tune_entry(Ctx& c, const SigmaPlan& P, int phase, int prec, double bytes) {
   const Ctx::TuneKey key{(const void*)P.fam->bra, (const void*)P.fam->ket, (const void*)P.fam->mpo, P.l, phase, prec};
   Ctx::TuneEntry& e = c.tune[key];
@@ -1567,7 +1732,7 @@ Ctx::TuneEntry& tune_entry(Ctx& c, const SigmaPlan& P, int phase, int prec, doub
 int tune_choice(const Ctx& c, const Ctx::TuneEntry& e) {
   if (!c.opts.autotune) return 0;
   if (e.best >= 0) return e.best;
-  for (int ci = 0; ci < 3; ++ci)
+  for (int ci = 0; ci < NSHAPE; ++ci)
     if (!(e.tried & (1 << ci))) return ci;
   return 0;
 }
@@ -1577,9 +1742,9 @@ void tune_record(Ctx& c, Ctx::TuneEntry& e, int ci, double ms) {
   if (!(e.tried & (1 << ci)) || ms < e.ms[ci]) e.ms[ci] = ms;
   e.tried |= 1 << ci;
   c.st.tune_trials++;
-  if (e.tried == 7) {
+  if (e.tried == (1 << NSHAPE) - 1) {
     int b = 0;
-    for (int ci2 = 1; ci2 < 3; ++ci2)
+    for (int ci2 = 1; ci2 < NSHAPE; ++ci2)
       if (e.ms[ci2] < e.ms[b]) b = ci2;
     e.best = b;
   }
@@ -1599,14 +1764,14 @@ void tc_sigma(Ctx& c, SigmaPlan& P, const double* x, double* y, int prec) {
   Ctx::TuneEntry& e1 = tune_entry(c, P, 1, prec, S->bytes1[v]);
   Ctx::TuneEntry& e2 = tune_entry(c, P, 2, prec, S->bytes2[v]);
   const int c1 = tune_choice(c, e1), c2 = tune_choice(c, e2);
-  build_lists(c, P, S, v, c1);
-  build_lists(c, P, S, v, c2);
-  const TcState::Lists& L1 = S->lists[v][c1];
-  const TcState::Lists& L2 = S->lists[v][c2];
+  build_lists(c, P, S, v, list_of(c1));
+  build_lists(c, P, S, v, list_of(c2));
+  const TcState::Lists& L1 = S->lists[v][list_of(c1)];
+  const TcState::Lists& L2 = S->lists[v][list_of(c2)];
   cudaEventRecord(c.ev_p0, c.s());
-  launch_tc(c, kp, (const TcTask*)L1.t1.p, L1.n1, L1.tiles1, (int*)S->err.p, TC_CAPS[c1]);
+  launch_tc(c, kp, (const TcTask*)L1.t1.p, L1.n1, L1.tiles1, (int*)S->err.p, TC_CAPS[c1], TC_CFG[c1]);
   cudaEventRecord(c.ev_p1, c.s());
-  launch_tc(c, kp, (const TcTask*)L2.t2.p, L2.n2, L2.tiles2, (int*)S->err.p, TC_CAPS[c2]);
+  launch_tc(c, kp, (const TcTask*)L2.t2.p, L2.n2, L2.tiles2, (int*)S->err.p, TC_CAPS[c2], TC_CFG[c2]);
   cudaEventRecord(c.ev_p2, c.s());
   launch_splitk_reduce_f32((const SplitSeg*)L2.segs.p, L2.nseg, L2.seg_tiles, (const float*)L2.ypart.p, y, c.s());
   cuda_check(cudaGetLastError(), "split-K reduction");

@@ -51,15 +51,19 @@ def test_wait_bound_expiry_returns_timeout(mpslcc):
 
 class _FlakyAllocator:
     """Device allocator over PyTorch's caching allocator that refuses its
-    N-th request (returns NULL), as an exhausted pool would."""
+    N-th request, as an exhausted pool would: it returns NULL, or raises (as
+    PyTorch's own allocator does when it runs out of memory)."""
 
-    def __init__(self, torch, stream):
+    def __init__(self, torch, stream, raise_on_failure=False):
         self.torch, self.stream = torch, stream
         self.count, self.fail_at, self.live = 0, None, {}
+        self.raise_on_failure = raise_on_failure
 
     def alloc(self, nbytes):
         self.count += 1
         if self.fail_at is not None and self.count == self.fail_at:
+            if self.raise_on_failure:
+                raise MemoryError("refused by the test allocator")
             return 0
         p = self.torch.cuda.caching_allocator_alloc(max(int(nbytes), 1), 0, self.stream)
         self.live[p] = nbytes
@@ -71,11 +75,12 @@ class _FlakyAllocator:
             self.torch.cuda.caching_allocator_delete(ptr)
 
 
-def test_failed_allocation_returns_nomem_and_context_recovers(mpslcc):
+@pytest.mark.parametrize("raise_on_failure", [False, True])
+def test_failed_allocation_returns_nomem_and_context_recovers(mpslcc, raise_on_failure):
     torch = pytest.importorskip("torch")
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream(0)
-    fa = _FlakyAllocator(torch, stream)
+    fa = _FlakyAllocator(torch, stream, raise_on_failure)
     c = synth.config(0)
     with mpslcc.Context(device=0, tol=1e-11, alloc=(fa.alloc, fa.free), stream=stream.cuda_stream) as ctx:
         ctx.build_mpo(c["h"], c["V"], 8, 0)
