@@ -78,7 +78,7 @@ def parse():
 
 # DRAM traffic per algorithmic byte of sigma phases 1 and 2 (split BF16),
 # measured by ncu on the kernel as it stands (see the roofline block)
-TRAFFIC_RATIO = (2.00, 1.19)
+TRAFFIC_RATIO = (1.41, 1.22)
 
 
 def peaks():
