@@ -841,6 +841,45 @@ struct ConvTask {
 };
 constexpr int CONV_CHUNK = 4096;
 
+// One converted element at output offset o (in the task's pattern).
+template <int PREC>
+__device__ __forceinline__ void conv_put(const ConvTask& T, long long o, double v) {
+  if (PREC == MPSLCC_TF32) {
+    ((float*)T.dst)[o] = (float)v;
+    return;
+  }
+  __nv_bfloat16* d = (__nv_bfloat16*)T.dst + o;
+  const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+  if (T.pattern == 0) {
+    d[0] = h;
+    return;
+  }
+  const double r1 = v - (double)__bfloat162float(h);
+  const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
+  const long long so = T.soff;
+  if (T.pattern == 1) {
+    d[0] = h;
+    d[so] = m;   // lo of the two-piece split: the rounded remainder
+    return;
+  }
+  const __nv_bfloat16 l = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(m)));
+  if (T.pattern == 2) {   // A side [h h m m h l]
+    d[0] = h;
+    d[so] = h;
+    d[2 * so] = m;
+    d[3 * so] = m;
+    d[4 * so] = h;
+    d[5 * so] = l;
+  } else {                // B side [h m m h l h]
+    d[0] = h;
+    d[so] = m;
+    d[2 * so] = m;
+    d[3 * so] = h;
+    d[4 * so] = l;
+    d[5 * so] = h;
+  }
+}
+
 template <int PREC>
 __global__ void conv_kernel(const ConvTask* __restrict__ t, int ntasks, long long total) {
   for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
@@ -857,39 +896,41 @@ __global__ void conv_kernel(const ConvTask* __restrict__ t, int ntasks, long lon
     const int b = (int)(local / per);
     const long long ch = local - (long long)b * per;
     const long long e1 = min(nel, (ch + 1) * CONV_CHUNK);
-    for (long long e = ch * CONV_CHUNK + threadIdx.x; e < e1; e += blockDim.x) {
-      int rr, cc;
-      double v;
-      if (T.trans) {  // consecutive threads walk the source row (coalesced reads)
-        cc = (int)(e / T.rows);
-        rr = (int)(e - (long long)cc * T.rows);
-        v = T.src[b * T.s_src + (long long)cc * T.src_ld + rr];
-      } else {
-        rr = (int)(e / T.cols);
-        cc = (int)(e - (long long)rr * T.cols);
-        v = T.src[b * T.s_src + (long long)rr * T.src_ld + cc];
+    const double* src = T.src + (long long)b * T.s_src;
+    const long long dbase = (long long)b * T.s_dst;
+    if (nel < (1LL << 31)) {
+      // 32-bit index arithmetic (a 64-bit division per element dominated
+      // this instruction-bound loop)
+      const int rows = T.rows, cols = T.cols;
+      const int e1i = (int)e1;
+      for (int e = (int)(ch * CONV_CHUNK) + (int)threadIdx.x; e < e1i; e += (int)blockDim.x) {
+        int rr, cc;
+        double v;
+        if (T.trans) {  // consecutive threads walk the source row (coalesced reads)
+          cc = e / rows;
+          rr = e - cc * rows;
+          v = src[(long long)cc * T.src_ld + rr];
+        } else {
+          rr = e / cols;
+          cc = e - rr * cols;
+          v = src[(long long)rr * T.src_ld + cc];
+        }
+        conv_put<PREC>(T, dbase + (long long)rr * T.dst_ld + cc, v);
       }
-      const long long o = b * T.s_dst + (long long)rr * T.dst_ld + cc;
-      if (PREC == MPSLCC_TF32) {
-        ((float*)T.dst)[o] = (float)v;
-      } else if (T.pattern == 0) {
-        ((__nv_bfloat16*)T.dst)[o] = __float2bfloat16_rn((float)v);
-      } else if (T.pattern == 1) {
-        __nv_bfloat16* d = (__nv_bfloat16*)T.dst + o;
-        const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-        const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
-        d[0] = h;
-        d[T.soff] = l;
-      } else {
-        __nv_bfloat16* d = (__nv_bfloat16*)T.dst + o;
-        const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
-        const double r1 = v - (double)__bfloat162float(h);
-        const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
-        const __nv_bfloat16 l = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(m)));
-        const __nv_bfloat16 pa[6] = {h, h, m, m, h, l}, pb[6] = {h, m, m, h, l, h};
-        const __nv_bfloat16* pp = T.pattern == 2 ? pa : pb;
-#pragma unroll
-        for (int j = 0; j < 6; ++j) d[j * T.soff] = pp[j];
+    } else {
+      for (long long e = ch * CONV_CHUNK + threadIdx.x; e < e1; e += blockDim.x) {
+        int rr, cc;
+        double v;
+        if (T.trans) {
+          cc = (int)(e / T.rows);
+          rr = (int)(e - (long long)cc * T.rows);
+          v = src[(long long)cc * T.src_ld + rr];
+        } else {
+          rr = (int)(e / T.cols);
+          cc = (int)(e - (long long)rr * T.cols);
+          v = src[(long long)rr * T.src_ld + cc];
+        }
+        conv_put<PREC>(T, dbase + (long long)rr * T.dst_ld + cc, v);
       }
     }
   }
@@ -1255,7 +1296,7 @@ void tc_prepare(Ctx& c, SigmaPlan& P, int prec) {
   S->mL = fused_piece_masks(W, lf.p, true);
   S->cstartL = W.bond[lf.p + 1].class_start;
   const std::vector<uint16_t> mR = rf.ext ? std::vector<uint16_t>() : fused_piece_masks(W, rf.p, false);
-  // piece-major K layout per bra key, every piece rounded up to 8 columns
+  // piece-major K layout per bra key, every piece rounded up to 16 columns
   S->K8.assign(nbk, 0);
   S->lcat_off.assign(nbk, 0);
   S->tt_off.assign(nbk, 0);
