@@ -11,6 +11,7 @@
 //   phase 2:  sigma = [L'_w1 | L'_w2 | ...] [T_w1 ; T_w2 ; ...]
 // so the sum over operator channels sits in the K dimension of one GEMM.
 #include "engine.hpp"
+#include "kruns.hpp"
 
 #include <cmath>
 #include <cstring>
@@ -919,21 +920,15 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
   // Every task's run table is {operand column, virtual start} pairs and a
   // sentinel; a task whose runs cover its K extent densely has none.
   std::vector<std::vector<int>> rt1, rt2;
-  auto add_runs = [](std::vector<std::pair<int, int>>& rg, int kext, std::vector<int>& tab) {
-    std::sort(rg.begin(), rg.end());
-    std::vector<std::pair<int, int>> m;   // merged [start, end)
-    for (const auto& x : rg) {
-      if (x.second <= x.first) continue;
-      if (!m.empty() && x.first <= m.back().second) m.back().second = std::max(m.back().second, x.second);
-      else m.push_back(x);
-    }
+  auto add_runs = [](std::vector<std::pair<long, long>>& rg, int kext, std::vector<int>& tab) {
+    const std::vector<std::pair<long, long>> m = merge_exact(rg);   // sorted, disjoint [start, end)
     tab.clear();
     int v = 0;
     for (const auto& x : m) {
       MPSLCC_REQUIRE(x.first >= 0 && x.second <= kext, ST_INTERNAL, "K run outside the operand");
-      tab.push_back(x.first);
+      tab.push_back((int)x.first);
       tab.push_back(v);
-      v += x.second - x.first;
+      v += (int)(x.second - x.first);
     }
     tab.push_back(0);
     tab.push_back(v);
@@ -957,7 +952,7 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
         int w1 = w + 1;
         while (w1 < S.nw && (rf.ext ? 1 : (mR[c0 + w1] >> (4 * so)) & 15) == in) ++w1;
         if (in) {
-          std::vector<std::pair<int, int>> rg;
+          std::vector<std::pair<long, long>> rg;
           for (int sn = 0; sn < 4; ++sn)
             if (in >> sn & 1) {
               const int o = piece_off(rf.FRk, fk, sn);
@@ -996,7 +991,7 @@ static void finish_sigma_plan(Ctx& c, SigmaPlan& P) {
     for (int so = 0; so < 4; ++so) {
       const int d = piece_dim(lf.FLb, fb, so);
       if (d == 0) continue;
-      std::vector<std::pair<int, int>> rg;
+      std::vector<std::pair<long, long>> rg;
       for (const auto& sg : lf.seg[bi]) {
         const int c0 = W.bond[lf.p + 1].class_start[sg.cls], fk = lf.kk[sg.kidx];
         for (int w = 0; w < sg.nw; ++w)

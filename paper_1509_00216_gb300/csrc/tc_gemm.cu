@@ -30,6 +30,7 @@
 #include <string>
 
 #include "engine.hpp"
+#include "kruns.hpp"
 
 namespace mpslcc {
 
@@ -1510,31 +1511,7 @@ constexpr int TC_CAPS[NSHAPE] = {256, 128, 64, 64};
 constexpr int TC_CFG[NSHAPE] = {0, 0, 0, 1};
 inline int list_of(int shape) { return shape < 3 ? shape : 2; }
 
-// K runs of one task: its non-zero columns come as ranges [a, b) of the
-// operands' K extent; each run starts on an 8-element boundary (16-byte TMA
-// coordinate) and is read in whole steps of KT columns.  A range that starts
-// before the open run's last step ends joins that run, so no column is read
-// by two runs; the columns a run reads outside its ranges are zero in the
-// operand whose zero pieces were skipped, so they add nothing.
-struct KRun { long kx, steps; };
-std::vector<KRun> merge_runs(std::vector<std::pair<long, long>>& r, int KT) {
-  std::sort(r.begin(), r.end());
-  std::vector<KRun> out;
-  long de = 0;
-  for (const auto& x : r) {
-    if (x.second <= x.first) continue;
-    const long a8 = x.first & ~7L;
-    if (!out.empty() && a8 < out.back().kx + out.back().steps * KT) {
-      de = std::max(de, x.second);
-      out.back().steps = (de - out.back().kx + KT - 1) / KT;
-    } else {
-      out.push_back({a8, (x.second - a8 + KT - 1) / KT});
-      de = x.second;
-    }
-  }
-  return out;
-}
-
+// K runs of a task: merge_runs (kruns.hpp).
 // Appends a task's run table (pairs {kx, steps before}, a sentinel, then the
 // run of each K split's first step) to `tab`; returns its offset.
 long append_runs(std::vector<int>& tab, const std::vector<KRun>& runs, int kchunk, int ksplit) {
