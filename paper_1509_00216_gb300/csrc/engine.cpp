@@ -596,21 +596,51 @@ void env_update_left(Ctx& c, Family& F, int p, const LeftFused& lf) {
   ne.data.alloc(&c, std::max(ne.size, 1L) * sizeof(double));
   c.scratch_a.ensure(&c, std::max(xsize, 1L) * sizeof(double));
   double* X = c.scratch_a.d();
-  std::vector<GemmTask> tx, ty;
+  // X_w = L'_w A_k over the non-zero local pieces of L'_w only: per run of
+  // channels with equal piece masks and per bra local state so, one product
+  // per ket state si the pieces reach.  The k-th si of a row block adds
+  // (beta = 1) in launch k, so no two tasks of one launch write the same
+  // rows; rows that no piece reaches stay zero.
+  cuda_check(cudaMemsetAsync(X, 0, std::max(xsize, 1L) * sizeof(double), c.s()), "env X zero");
+  const std::vector<uint16_t> mL = fused_piece_masks(*F.mpo, p, true);
+  std::vector<std::vector<GemmTask>> tx(4);
+  std::vector<GemmTask> ty;
   for (const auto& j : jobs) {
-    int rows = lf.FLb.d[j.fb];
-    int dk = bk.d[j.ik], db = bb.d[j.ib];
-    long K = lf.K[j.bkey];
+    const int rows = lf.FLb.d[j.fb];
+    const int dk = bk.d[j.ik], db = bb.d[j.ib];
+    const long K = lf.K[j.bkey];
+    const int width = j.sg->width, c0 = mb.class_start[j.sg->cls];
     const double* Lp = lf.data.d() + lf.off[j.bkey] + j.sg->koff;
     const double* Ak = Kt.site[p].lf.d() + Kt.site[p].lf_off[j.ik];
     const double* Ab = B.site[p].lf.d() + B.site[p].lf_off[j.ib];
-    tx.push_back(gemm(Lp, Ak, X + j.xoff, rows, dk, j.sg->width, (int)K, dk, dk, 0, j.sg->nw, j.sg->width, 0,
-                      (long long)rows * dk));
+    for (int w = 0; w < j.sg->nw;) {
+      const uint16_t m = mL[c0 + w];
+      int w1 = w + 1;
+      while (w1 < j.sg->nw && mL[c0 + w1] == m) ++w1;
+      for (int so = 0; so < 4; ++so) {
+        const int dso = piece_dim(lf.FLb, j.fb, so);
+        if (dso == 0) continue;
+        const long ro = piece_off(lf.FLb, j.fb, so);
+        int k = 0;
+        for (int si = 0; si < 4; ++si) {
+          if (!((m >> (4 * so + si)) & 1)) continue;
+          const int dsi = piece_dim(lf.FLk, j.fk, si);
+          if (dsi == 0) continue;
+          const long co = piece_off(lf.FLk, j.fk, si);
+          tx[k].push_back(gemm(Lp + ro * K + (long)w * width + co, Ak + co * dk, X + j.xoff + (long)w * rows * dk + ro * dk,
+                               dso, dk, dsi, (int)K, dk, dk, 0, w1 - w, width, 0, (long long)rows * dk, 1.0,
+                               k > 0 ? 1.0 : 0.0));
+          c.st.env_flops += 2.0 * (w1 - w) * (double)dso * dk * dsi;
+          ++k;
+        }
+      }
+      w = w1;
+    }
     ty.push_back(gemm(Ab, X + j.xoff, ne.data.d() + j.eoff, db, dk, rows, db, dk, dk, GEMM_TA, j.sg->nw, 0,
                       (long long)rows * dk, (long long)db * dk));
-    c.st.env_flops += 2.0 * j.sg->nw * ((double)rows * dk * j.sg->width + (double)db * dk * rows);
+    c.st.env_flops += 2.0 * j.sg->nw * (double)db * dk * rows;
   }
-  run_gemm_tasks(c, tx);
+  for (auto& t : tx) run_gemm_tasks(c, t);
   run_gemm_tasks(c, ty);
   ne.valid = true;
   F.L[p + 1] = std::move(ne);
@@ -649,20 +679,55 @@ void env_update_right(Ctx& c, Family& F, int p, const RightFused& rf) {
   ne.data.alloc(&c, std::max(ne.size, 1L) * sizeof(double));
   c.scratch_a.ensure(&c, std::max(ysize, 1L) * sizeof(double));
   double* Y = c.scratch_a.d();
-  std::vector<GemmTask> ty, tz;
+  // Y_w = R'_w B_k^T over the non-zero local pieces of R'_w only (as for the
+  // left side); a one-site position's right side (the environment itself,
+  // one piece per sector) keeps the dense product
+  const bool pieces = !rf.ext;
+  if (pieces) cuda_check(cudaMemsetAsync(Y, 0, std::max(ysize, 1L) * sizeof(double), c.s()), "env Y zero");
+  const std::vector<uint16_t> mR = pieces ? fused_piece_masks(*F.mpo, p, false) : std::vector<uint16_t>();
+  std::vector<std::vector<GemmTask>> ty(4);
+  std::vector<GemmTask> tz;
   for (const auto& j : jobs) {
-    int rb = rf.FRb.d[j.fb], rk = rf.FRk.d[j.fk];
-    int dk = bk.d[j.ik], db = bb.d[j.ib];
-    long blkS = (long)rb * rk;
+    const int rb = rf.FRb.d[j.fb], rk = rf.FRk.d[j.fk];
+    const int dk = bk.d[j.ik], db = bb.d[j.ib];
+    const long blkS = (long)rb * rk;
     const double* Rp = rf.base() + j.S->off;
     const double* Bk = Kt.site[p].rf.d() + Kt.site[p].rf_off[j.ik];
     const double* Bb = B.site[p].rf.d() + B.site[p].rf_off[j.ib];
-    ty.push_back(gemm(Rp, Bk, Y + j.yoff, rb, dk, rk, rk, rk, dk, GEMM_TB, j.S->nw, blkS, 0, (long long)rb * dk));
+    if (!pieces) {
+      ty[0].push_back(gemm(Rp, Bk, Y + j.yoff, rb, dk, rk, rk, rk, dk, GEMM_TB, j.S->nw, blkS, 0, (long long)rb * dk));
+      c.st.env_flops += 2.0 * j.S->nw * (double)rb * dk * rk;
+    } else {
+      const int c0 = mb.class_start[j.S->cls];
+      for (int w = 0; w < j.S->nw;) {
+        const uint16_t m = mR[c0 + w];
+        int w1 = w + 1;
+        while (w1 < j.S->nw && mR[c0 + w1] == m) ++w1;
+        for (int so = 0; so < 4; ++so) {
+          const int dso = piece_dim(rf.FRb, j.fb, so);
+          if (dso == 0) continue;
+          const long ro = piece_off(rf.FRb, j.fb, so);
+          int k = 0;
+          for (int si = 0; si < 4; ++si) {
+            if (!((m >> (4 * so + si)) & 1)) continue;
+            const int dsi = piece_dim(rf.FRk, j.fk, si);
+            if (dsi == 0) continue;
+            const long co = piece_off(rf.FRk, j.fk, si);
+            ty[k].push_back(gemm(Rp + ((long)w * rb + ro) * rk + co, Bk + co, Y + j.yoff + (long)w * rb * dk + ro * dk,
+                                 dso, dk, dsi, rk, rk, dk, GEMM_TB, w1 - w, blkS, 0, (long long)rb * dk, 1.0,
+                                 k > 0 ? 1.0 : 0.0));
+            c.st.env_flops += 2.0 * (w1 - w) * (double)dso * dk * dsi;
+            ++k;
+          }
+        }
+        w = w1;
+      }
+    }
     tz.push_back(gemm(Bb, Y + j.yoff, ne.data.d() + j.eoff, db, dk, rb, rb, dk, dk, 0, j.S->nw, 0,
                       (long long)rb * dk, (long long)db * dk));
-    c.st.env_flops += 2.0 * j.S->nw * ((double)rb * dk * rk + (double)db * dk * rb);
+    c.st.env_flops += 2.0 * j.S->nw * (double)db * dk * rb;
   }
-  run_gemm_tasks(c, ty);
+  for (auto& t : ty) run_gemm_tasks(c, t);
   run_gemm_tasks(c, tz);
   ne.valid = true;
   F.R[p] = std::move(ne);
