@@ -81,6 +81,22 @@ def parse():
 TRAFFIC_RATIO = (1.41, 1.22)
 
 
+def max_over_ranks(vals, td, device):
+    """Element-wise maximum of per-rank timings over the process group: the
+    slowest rank sets the job's time."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_value(world, flops_per_rank, seconds):
+    """Whole-job throughput in TFLOP/s: every rank runs the same workload
+    (replicas, weak scaling), so the job processes world x one rank's flops in
+    the slowest rank's time."""
+    return world * flops_per_rank / seconds / 1e12
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -447,9 +463,7 @@ def gpu_arm(args, rank, world, local_rank):
     if dist:
         td.barrier()
     if dist:
-        t = torch.tensor([dev_s, e2e_s], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        dev_s, e2e_s = t.tolist()
+        dev_s, e2e_s = max_over_ranks([dev_s, e2e_s], td, "cuda")
     pk = peaks()
     kern = sweep_sigma_s
     if prec == 0:
@@ -484,7 +498,7 @@ def gpu_arm(args, rank, world, local_rank):
     else:
         roof["traffic"] = None
     roof["peak_source"] = pk["src"]
-    value = world * flops / dev_s / 1e12
+    value = job_value(world, flops, dev_s)
     line = dict(metric=METRIC, value=value, unit="TFLOP/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=dev_s / args.steps * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype={0: "f64", 1: "tf32", 2: "bf16", 3: "bf16x3"}[prec], data="synthetic",
@@ -497,7 +511,7 @@ def gpu_arm(args, rank, world, local_rank):
                 solver={"noconv": st["n_noconv"], "indefinite": st["n_indefinite"], "j_rise": st["n_j_rise"],
                         "max_rel_residual": st["max_rel_residual"]},
                 roofline=roof, gpu_launches=st["kernel_launches"],
-                e2e={"value": world * flops2 / e2e_s / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                e2e={"value": job_value(world, flops2, e2e_s), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                      "d2h_bytes_per_step": d2h, "s_per_step": e2e_s / args.steps,
                      "what": "host wall time of the public call mpslcc_lcc_sweep per step (E2 read back)"},
                 energy_eval_s=energy_eval_s)
